@@ -1,0 +1,230 @@
+"""Seeded synthetic workloads shaped like the paper's scenes.
+
+This module only draws inputs: particle positions, initial velocities, material
+constants and rigid-body descriptions.  It holds none of the method's arithmetic,
+so both the CUDA library and the FP64 oracle consume exactly the same FP32 input
+values from it.
+
+Every workload is a plain dict:
+  n            grid nodes per dimension (dx = 1/n, domain [0,1)^3)
+  x, v         float32 (N,3) positions and initial velocities
+  E, nu        float32 (N,) Young's modulus and Poisson ratio per particle
+  rho, V0      density and initial particle volume (mass = rho * V0)
+  model        "fixed_corotated" | "neo_hookean"
+  plasticity   bool (von Mises), yield_stress
+  dt, substeps time step and number of substeps of the scene
+  gravity      3-vector; bound boundary width in nodes; floor_sticky bool
+  rigids       list of rigid descriptions (dicts), see ``quad_slicer`` etc.
+
+The falling-cube shape follows the paper's timing scene (Sec. III-D: a cube
+falling under gravity); the tissue slab, blade ("slicer", Sec. IV-B) and
+capsule-chain thread ("connected line segments", Sec. IV-C) follow the cutting
+and suturing scenes of Sec. VI.  The paper gives no tissue constants, sizes or
+particle counts for those scenes, so the numbers below are proposed values.
+"""
+import math
+
+import numpy as np
+
+SEED_BASE = 2502_18437
+
+
+def rng(tag: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(SEED_BASE + int(tag)))
+
+
+def _f32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def _scene(n, x, v, E, nu, *, rho, V0, model, dt, substeps, plasticity=False, yield_stress=0.0,
+           rigids=(), gravity=(0.0, -9.8, 0.0), bound=3, floor_sticky=True, name=""):
+    N = len(x)
+    return dict(name=name, n=int(n), x=_f32(x).reshape(N, 3), v=_f32(v).reshape(N, 3),
+                E=_f32(np.broadcast_to(E, (N,))), nu=_f32(np.broadcast_to(nu, (N,))),
+                rho=float(rho), V0=float(np.float32(V0)), model=model, plasticity=bool(plasticity),
+                yield_stress=float(yield_stress), dt=float(dt), substeps=int(substeps),
+                gravity=tuple(float(g) for g in gravity), bound=int(bound),
+                floor_sticky=bool(floor_sticky), rigids=list(rigids))
+
+
+# ----------------------------------------------------------- rigid bodies
+
+def quad_slicer(center, quat, *, half_edge, half_depth, thickness, vel=(0, 0, 0), omega=(0, 0, 0),
+                mu_k=0.3, c_d=1.0, margin=0.0, spine_radius=None):
+    """Blade: body x along the cutting edge, body y from the spine to the edge,
+    body z the blade normal; half sizes half_edge (x) and half_depth (y)."""
+    return dict(type="quad_slicer", center=tuple(center), quat=tuple(quat), vel=tuple(vel),
+                omega=tuple(omega), mu_k=mu_k, c_d=c_d, margin=margin,
+                half=(half_edge, half_depth, 0.0), thickness=thickness,
+                spine_radius=0.5 * thickness if spine_radius is None else spine_radius)
+
+
+def segments(center, quat, pts, *, radius, vel=(0, 0, 0), omega=(0, 0, 0), mu_k=0.3, c_d=1.0,
+             margin=0.0):
+    """Chain of connected capsules through ``pts`` (body frame)."""
+    return dict(type="segments", center=tuple(center), quat=tuple(quat), pts=np.asarray(pts, float),
+                radius=radius, vel=tuple(vel), omega=tuple(omega), mu_k=mu_k, c_d=c_d, margin=margin)
+
+
+def sphere(center, radius, *, vel=(0, 0, 0), omega=(0, 0, 0), mu_k=0.3, c_d=1.0, margin=0.0,
+           quat=(1, 0, 0, 0)):
+    return dict(type="sphere", center=tuple(center), quat=tuple(quat), radius=radius, vel=tuple(vel),
+                omega=tuple(omega), mu_k=mu_k, c_d=c_d, margin=margin)
+
+
+def box(center, half, *, quat=(1, 0, 0, 0), vel=(0, 0, 0), omega=(0, 0, 0), mu_k=0.3, c_d=1.0,
+        margin=0.0):
+    return dict(type="box", center=tuple(center), quat=tuple(quat), half=tuple(half), vel=tuple(vel),
+                omega=tuple(omega), mu_k=mu_k, c_d=c_d, margin=margin)
+
+
+# Blade orientation with the edge along world z, the edge pointing down (-y)
+# and the blade normal along world x: a half turn about (1,0,1)/sqrt(2).
+BLADE_EDGE_Z_DOWN = (0.0, math.sqrt(0.5), 0.0, math.sqrt(0.5))
+
+
+def _yaw_blade_quat(yaw):
+    """Blade edge down, rotated by ``yaw`` about world y."""
+    qy = np.array([math.cos(yaw / 2), 0.0, math.sin(yaw / 2), 0.0])
+    qb = np.array(BLADE_EDGE_Z_DOWN)
+    w1, x1, y1, z1 = qy
+    w2, x2, y2, z2 = qb
+    return (w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2, w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+            w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2, w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2)
+
+
+# -------------------------------------------------------------- workloads
+
+def lattice_cube(n_side, spacing, corner):
+    i = (np.arange(n_side) + 0.5) * spacing
+    g = np.stack(np.meshgrid(i, i, i, indexing="ij"), -1).reshape(-1, 3)
+    return g + np.asarray(corner, float)
+
+
+def elastic_cube(n=32, n_side=16, corner=(0.375, 0.1, 0.375), substeps=100, v0=(0.0, 0.0, 0.0),
+                 E=1e4, nu=0.3, rho=1.0, dt=1e-4, gravity=(0.0, -9.8, 0.0), model="fixed_corotated"):
+    """Falling elastic cube: 16^3 lattice at spacing dx/2 (8 particles per cell)
+    on a 32^3 grid, fixed-corotated E=1e4 nu=0.3 rho=1, dt=1e-4, sticky floor."""
+    dx = 1.0 / n
+    x = lattice_cube(n_side, dx / 2, corner)
+    V0 = (dx / 2) ** 3
+    v = np.broadcast_to(np.asarray(v0, float), x.shape)
+    return _scene(n, x, v, E, nu, rho=rho, V0=V0, model=model, dt=dt, substeps=substeps,
+                  gravity=gravity, name=f"elastic_cube_{len(x)}p_n{n}")
+
+
+def tissue_slab(cells=(128, 16, 128), lo=(0.25, 0.03, 0.25), size=(0.5, 0.1, 0.5), n=128, seed=1,
+                substeps=1000, with_tools=True, dt=1e-4):
+    """Tissue slab for cutting/suturing: one uniform point per jitter cell in a
+    0.5 x 0.1 x 0.5 box, Neo-Hookean, E ~ U[5e3, 2e4], nu = 0.4, rho = 1000,
+    driven by a thin blade (0.002 thick, 0.1 m/s down) and a 32-capsule thread
+    (radius 0.003) sliding along its own axis at 0.05 m/s."""
+    g = rng(seed)
+    cells = np.asarray(cells)
+    N = int(np.prod(cells))
+    idx = np.stack(np.meshgrid(*[np.arange(c) for c in cells], indexing="ij"), -1).reshape(-1, 3)
+    h = np.asarray(size) / cells
+    x = np.asarray(lo) + (idx + g.random((N, 3))) * h
+    E = g.uniform(5e3, 2e4, N)
+    V0 = float(np.prod(size)) / N
+    dx = 1.0 / n
+    rigids = []
+    if with_tools:
+        cx, cz = lo[0] + size[0] / 2, lo[2] + size[2] / 2
+        top = lo[1] + size[1]
+        half_edge, half_depth = 0.3 * size[2], 0.08 * size[1] / 0.1 / 2
+        edge_y = top - 0.01
+        rigids.append(quad_slicer((cx, edge_y + half_depth, cz), BLADE_EDGE_Z_DOWN, half_edge=half_edge,
+                                  half_depth=half_depth, thickness=0.002, vel=(0.0, -0.1, 0.0),
+                                  mu_k=0.3, c_d=1.0, margin=dx))
+        L = 0.8 * size[0]
+        pts = np.stack([np.linspace(-L / 2, L / 2, 33), np.zeros(33), np.zeros(33)], -1)
+        rigids.append(segments((cx, lo[1] + 0.5 * size[1], cz), (1, 0, 0, 0), pts, radius=0.003,
+                               vel=(0.05, 0.0, 0.0), mu_k=0.3, c_d=1.0, margin=dx))
+    return _scene(n, x, np.zeros((N, 3)), E, 0.4, rho=1000.0, V0=V0, model="neo_hookean", dt=dt,
+                  substeps=substeps, rigids=rigids, name=f"tissue_slab_{N}p_n{n}")
+
+
+SCALE_POINTS = {65536: 64, 262144: 128, 1048576: 256, 4194304: 256}
+
+
+def tissue_block(N=1048576, n=None, seed=2, substeps=500, dt=5e-5, plasticity=True):
+    """Scale-sweep block: N uniform points (8 per cell on average) in an
+    axis-aligned cube of side (N/8)^(1/3) dx, centred in x and z with its bottom
+    at y = 0.03, falling at 2 m/s onto the sticky floor; fixed-corotated
+    E = 1e4, nu = 0.3, rho = 1000, von Mises yield 50."""
+    if n is None:
+        n = SCALE_POINTS.get(N, 256)
+    dx = 1.0 / n
+    side = (N / 8.0) ** (1.0 / 3.0) * dx
+    g = rng(seed + 1000 * (N % 997))
+    lo = np.array([0.5 - side / 2, 0.03, 0.5 - side / 2])
+    x = lo + g.random((N, 3)) * side
+    V0 = side ** 3 / N
+    v = np.broadcast_to(np.array([0.0, -2.0, 0.0]), (N, 3))
+    return _scene(n, x, v, 1e4, 0.3, rho=1000.0, V0=V0, model="fixed_corotated", dt=dt,
+                  substeps=substeps, plasticity=plasticity, yield_stress=50.0,
+                  name=f"tissue_block_{N}p_n{n}")
+
+
+def diff_cube(n=64, n_side=32, seed=3, substeps=200, model="fixed_corotated", dt=1e-4):
+    """Differentiable workload: 32^3 lattice at 8 particles per cell on a 64^3
+    grid (cube side 0.25, centred), rho = 1000, E ~ U[5e3, 2e4], nu ~ U[0.25, 0.4],
+    v0 = a + B (x - c) + N(0, 0.01^2) with seeded a, B (|B| ~ 1/s); no rigids and
+    no wall contact.  Also returns the loss target (centre + seeded offset)."""
+    g = rng(seed)
+    dx = 1.0 / n
+    side = n_side * dx / 2
+    c = np.array([0.5, 0.5, 0.5])
+    x = lattice_cube(n_side, dx / 2, c - side / 2)
+    N = len(x)
+    E = g.uniform(5e3, 2e4, N)
+    nu = g.uniform(0.25, 0.4, N)
+    a = g.normal(0, 0.1, 3)
+    B = g.normal(0, 1.0 / math.sqrt(3.0), (3, 3))
+    v = a + (x - c) @ B.T + g.normal(0, 0.01, (N, 3))
+    sc = _scene(n, x, v, E, nu, rho=1000.0, V0=(dx / 2) ** 3, model=model, dt=dt, substeps=substeps,
+                name=f"diff_cube_{N}p_n{n}")
+    sc["target"] = tuple(float(t) for t in (c + g.normal(0, 0.01, 3)))
+    return sc
+
+
+def batched_scenes(n_scenes=256, seed=4, lo_count=2048, hi_count=32768, substeps=1000, dt=1e-4):
+    """Batched workload: scenes with particle counts log-uniform in [2k, 32k],
+    grid 64^3 when the count exceeds 16k and otherwise a coin flip between
+    32^3 and 64^3; a tissue block at 8 particles per cell resting above the
+    sticky floor and one blade per scene with seeded yaw in [0, pi), position
+    within 0.05 of the block centre and downward speed U[0.05, 0.2] m/s;
+    fixed-corotated E = 1e4, nu = 0.3, rho = 1000, dt = 1e-4."""
+    g = rng(seed)
+    scenes = []
+    for s in range(n_scenes):
+        N = int(round(math.exp(g.uniform(math.log(lo_count), math.log(hi_count)))))
+        n = 64 if N > 16384 else int(g.choice([32, 64]))
+        dx = 1.0 / n
+        side = (N / 8.0 / 0.5) ** (1.0 / 3.0) * dx  # block side x side/2 x side
+        size = np.array([side, side / 2, side])
+        lo = np.array([0.5 - side / 2, 4.0 * dx, 0.5 - side / 2])
+        x = lo + g.random((N, 3)) * size
+        yaw = g.uniform(0.0, math.pi)
+        off = g.uniform(-0.05, 0.05, 2)
+        speed = g.uniform(0.05, 0.2)
+        top = lo[1] + size[1]
+        half_depth = 0.05
+        blade = quad_slicer((0.5 + off[0], top + 0.005 + half_depth, 0.5 + off[1]), _yaw_blade_quat(yaw),
+                            half_edge=0.3 * side, half_depth=half_depth, thickness=0.002,
+                            vel=(0.0, -speed, 0.0), mu_k=0.3, c_d=1.0, margin=dx)
+        scenes.append(_scene(n, x, np.zeros((N, 3)), 1e4, 0.3, rho=1000.0, V0=float(np.prod(size)) / N,
+                             model="fixed_corotated", dt=dt, substeps=substeps, rigids=[blade],
+                             name=f"batched_{s}"))
+    return scenes
+
+
+def scaled_copy(sc, keep):
+    """The first ``keep`` particles of a scene (a bounded sample of it)."""
+    out = dict(sc)
+    for k in ("x", "v", "E", "nu"):
+        out[k] = np.ascontiguousarray(sc[k][:keep])
+    out["name"] = sc["name"] + f"_sample{keep}"
+    return out
