@@ -310,3 +310,25 @@ def sort_by_brick(n, x32):
 def loss(x, v, target):
     x, v, t = _arr(x).reshape(-1, 3), _arr(v).reshape(-1, 3), _arr(target, (3,))
     return lib().orc_loss(len(x), _dp(x), _dp(v), _dp(t))
+
+
+# ------------------------------------------------- workload marshalling
+
+def lame_arrays(E, nu):
+    """Lame parameters of per-particle (E, nu), the textbook formula of orc_lame."""
+    E = np.asarray(E, dtype=np.float64)
+    nu = np.asarray(nu, dtype=np.float64)
+    return E / (2.0 * (1.0 + nu)), E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+
+
+def config_from_workload(sc):
+    """Oracle config of a workload dict (mass = rho * V0 rounded as in FP32 inputs)."""
+    m_p = float(np.float32(sc["rho"]) * np.float32(sc["V0"]))
+    return make_config(sc["n"], m_p, sc["V0"], bound=sc["bound"], floor_sticky=sc["floor_sticky"],
+                       model=sc["model"], plasticity=sc["plasticity"], yield_stress=sc["yield_stress"],
+                       gravity=sc["gravity"])
+
+
+def state_from_workload(sc, x=None, v=None, C=None, F=None):
+    mu, lam = lame_arrays(sc["E"], sc["nu"])
+    return State(sc["x"] if x is None else x, sc["v"] if v is None else v, C, F, mu, lam)

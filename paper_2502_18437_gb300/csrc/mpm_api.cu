@@ -1,0 +1,831 @@
+// C ABI of the MLS-MPM library (include/mpm.h): context lifecycle, factory
+// calls, substep scheduling with CUDA-graph replay, blocking state readback.
+//
+// Object model after Sec. V-A of arXiv 2502.18437: mpm_substep is the
+// asynchronous Scene::advance (everything is enqueued on the context's
+// stream), mpm_read_state the blocking Scene::fetchResults.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <thread>
+
+#include "mpm_ctx.cuh"
+
+using namespace mpm;
+
+namespace mpm {
+
+int status_from_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess) return MPM_OK;
+    if (e == cudaErrorMemoryAllocation) return MPM_ERR_OUT_OF_MEMORY;
+    return MPM_ERR_CUDA;
+}
+
+#define MPM_CK(call)                                      \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return status_from_cuda(e_); \
+    } while (0)
+
+static int timeout_ms(const mpm_ctx* c) { return c->cfg.timeout_ms > 0 ? c->cfg.timeout_ms : 10000; }
+
+// Wait for all work enqueued on the context's stream, polling an event with a
+// bound instead of blocking inside the driver.
+int wait_stream(mpm_ctx* c)
+{
+    MPM_CK(cudaEventRecord(c->ev, c->stream));
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaEventQuery(c->ev);
+        if (e == cudaSuccess) return MPM_OK;
+        if (e != cudaErrorNotReady) return status_from_cuda(e);
+        const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+        if (ms > timeout_ms(c)) return MPM_ERR_TIMEOUT;
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+size_t state_bytes(int cap) { return (size_t)cap * (26 * sizeof(float) + sizeof(int)); }
+
+PState state_view(float* base, int cap)
+{
+    PState s;
+    s.x = base;
+    s.v = base + 3 * (size_t)cap;
+    s.C = base + 6 * (size_t)cap;
+    s.F = base + 15 * (size_t)cap;
+    s.mu = base + 24 * (size_t)cap;
+    s.lam = base + 25 * (size_t)cap;
+    s.id = reinterpret_cast<int*>(base + 26 * (size_t)cap);
+    return s;
+}
+
+int ensure_stage(mpm_ctx* c, size_t bytes)
+{
+    if (bytes <= c->stage_bytes) return MPM_OK;
+    if (c->d_stage) {
+        MPM_CK(cudaStreamSynchronize(c->stream));
+        cudaFree(c->d_stage);
+        c->d_stage = nullptr;
+        c->stage_bytes = 0;
+    }
+    MPM_CK(cudaMalloc(&c->d_stage, bytes));
+    c->stage_bytes = bytes;
+    return MPM_OK;
+}
+
+static int ensure_pinned(mpm_ctx* c, size_t bytes)
+{
+    if (bytes <= c->pinned_bytes) return MPM_OK;
+    if (c->h_pinned) {
+        MPM_CK(cudaStreamSynchronize(c->stream));
+        cudaFreeHost(c->h_pinned);
+        c->h_pinned = nullptr;
+        c->pinned_bytes = 0;
+    }
+    MPM_CK(cudaMallocHost(&c->h_pinned, bytes));
+    c->pinned_bytes = bytes;
+    return MPM_OK;
+}
+
+static bool is_pinned_host(const void* p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost;
+}
+
+int upload_scenes(mpm_ctx* c)
+{
+    if (!c->scenes_dirty) return MPM_OK;
+    MPM_CK(cudaMemcpyAsync(c->d_scenes, c->h_scenes.data(), sizeof(SceneDev) * c->n_scenes, cudaMemcpyHostToDevice,
+                           c->stream));
+    c->scenes_dirty = false;
+    return MPM_OK;
+}
+
+void clear_graphs(mpm_ctx* c)
+{
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+}
+
+static int persistent_ctas(mpm_ctx* c)
+{
+    int occ = std::min(occupancy_p2g(c->p2g_threads), occupancy_g2p(c->g2p_threads));
+    if (occ < 1) occ = 1;
+    if (c->ctas_per_sm > 0 && c->ctas_per_sm < occ) occ = c->ctas_per_sm;
+    return c->num_sms * occ;
+}
+
+StepArgs step_args(mpm_ctx* c, float dt, int s0, int s1, const PState& in, const PState& out)
+{
+    StepArgs a{};
+    a.r.s0 = s0;
+    a.r.s1 = s1;
+    a.r.bb0 = c->brick_base[s0];
+    a.r.nbr = c->brick_base[s1] - c->brick_base[s0];
+    a.r.p0 = c->h_scenes[s0].p_begin;
+    int pend = s1 < c->n_scenes ? c->h_scenes[s1].p_begin : c->total_particles;
+    a.r.np = pend - a.r.p0;
+    a.sb = c->sb;
+    a.scenes = c->d_scenes;
+    a.rigids = c->d_rigids;
+    a.impulse = c->d_impulse;
+    a.t_scene = c->d_time;
+    a.epoch = c->d_epoch;
+    a.brick_epoch = c->brick_epoch;
+    a.err = c->d_err;
+    a.G = c->G;
+    a.V = c->V;
+    a.in = in;
+    a.out = out;
+    a.cap = c->cap;
+    a.dt = dt;
+    for (int i = 0; i < 3; ++i) a.gravity[i] = c->cfg.gravity[i];
+    a.bound = c->cfg.bound;
+    a.floor_sticky = c->cfg.floor_sticky;
+    a.model = c->cfg.model;
+    a.plasticity = c->cfg.plasticity;
+    a.yield_stress = c->cfg.yield_stress;
+    a.persistent_ctas = persistent_ctas(c);
+    a.p2g_threads = c->p2g_threads;
+    a.g2p_threads = c->g2p_threads;
+    return a;
+}
+
+// One substep of every scene: sort, P2G, grid update, G2P.
+int enqueue_substep(mpm_ctx* c, float dt, const PState& in, const PState& out)
+{
+    const int groups = c->launch_mode == 1 ? c->n_scenes : 1;
+    for (int g = 0; g < groups; ++g) {
+        const int s0 = c->launch_mode == 1 ? g : 0;
+        const int s1 = c->launch_mode == 1 ? g + 1 : c->n_scenes;
+        StepArgs a = step_args(c, dt, s0, s1, in, out);
+        cudaEvent_t* ev = nullptr;
+        if (c->phase_timing) {
+            if (c->phase_used + 5 > c->phase_events.size()) {
+                for (int k = 0; k < 5 * 64; ++k) {
+                    cudaEvent_t e;
+                    MPM_CK(cudaEventCreate(&e));
+                    c->phase_events.push_back(e);
+                }
+            }
+            ev = &c->phase_events[c->phase_used];
+            c->phase_used += 5;
+        }
+        if (ev) MPM_CK(cudaEventRecord(ev[0], c->stream));
+        MPM_CK(launch_sort(a, c->stream));
+        if (ev) MPM_CK(cudaEventRecord(ev[1], c->stream));
+        MPM_CK(launch_p2g(a, c->stream));
+        if (ev) MPM_CK(cudaEventRecord(ev[2], c->stream));
+        MPM_CK(launch_grid(a, c->stream));
+        if (ev) MPM_CK(cudaEventRecord(ev[3], c->stream));
+        MPM_CK(launch_g2p(a, c->stream));
+        if (ev) MPM_CK(cudaEventRecord(ev[4], c->stream));
+    }
+    return MPM_OK;
+}
+
+int ensure_keys(mpm_ctx* c)
+{
+    if (c->keys_valid) return MPM_OK;
+    MPM_CK(cudaMemsetAsync(c->sb.cnt, 0, sizeof(int) * (size_t)c->total_bricks, c->stream));
+    StepArgs a = step_args(c, 0.f, 0, c->n_scenes, c->st[c->cur], c->st[c->cur ^ 1]);
+    MPM_CK(launch_init_keys(a, c->st[c->cur], c->stream));
+    c->keys_valid = true;
+    return MPM_OK;
+}
+
+}  // namespace mpm
+
+// ===================================================================== ABI
+
+extern "C" const char* mpm_status_string(int s)
+{
+    switch (s) {
+    case MPM_OK: return "ok";
+    case MPM_ERR_INVALID_ARGUMENT: return "invalid argument";
+    case MPM_ERR_OUT_OF_MEMORY: return "out of memory";
+    case MPM_ERR_CUDA: return "CUDA runtime error";
+    case MPM_ERR_OUT_OF_DOMAIN: return "a particle left its scene's grid";
+    case MPM_ERR_NONFINITE: return "a particle value became non-finite";
+    case MPM_ERR_INVERTED: return "inverted element (det F <= 0) where the law needs ln J";
+    case MPM_ERR_CAPACITY: return "particle capacity exceeded";
+    case MPM_ERR_TIMEOUT: return "bounded wait timed out";
+    case MPM_ERR_STATE: return "call out of order";
+    default: return "unknown status";
+    }
+}
+
+static void free_ctx(mpm_ctx* c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    mpm_tape_free(c);
+    clear_graphs(c);
+    for (int i = 0; i < 2; ++i) cudaFree(c->state_mem[i]);
+    void* bufs[] = {c->sb.key, c->sb.rank, c->sb.perm, c->sb.cnt, c->sb.off, c->sb.act_brick, c->sb.act_start,
+                    c->sb.act_count, c->sb.act_scene, c->sb.nact_brick, c->sb.nact_scene, c->sb.counters,
+                    c->sb.tile_status, c->sb.tile_agg, c->sb.tile_incl, c->G, c->V, c->brick_epoch,
+                    c->d_scenes, c->d_rigids, c->d_impulse, c->d_err, c->d_time, c->d_epoch, c->d_stage};
+    for (void* p : bufs) cudaFree(p);
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    if (c->ev) cudaEventDestroy(c->ev);
+    for (cudaEvent_t e : c->phase_events) cudaEventDestroy(e);
+    delete c;
+}
+
+extern "C" int mpm_destroy(mpm_ctx* c);
+
+extern "C" int mpm_create(const mpm_config* cfg, void* stream, mpm_ctx** out)
+{
+    if (!cfg || !out) return MPM_ERR_INVALID_ARGUMENT;
+    *out = nullptr;
+    if (cfg->n_scenes < 1 || cfg->max_particles < 0 || cfg->max_particles > (int64_t)1 << 30) return MPM_ERR_INVALID_ARGUMENT;
+    if (cfg->model != MPM_FIXED_COROTATED && cfg->model != MPM_NEO_HOOKEAN) return MPM_ERR_INVALID_ARGUMENT;
+    if (cfg->plasticity != MPM_PLASTIC_NONE && cfg->plasticity != MPM_PLASTIC_VON_MISES) return MPM_ERR_INVALID_ARGUMENT;
+    if (cfg->bound < 0) return MPM_ERR_INVALID_ARGUMENT;
+    mpm_ctx* c = new mpm_ctx();
+    c->cfg = *cfg;
+    c->cfg.scene_grid_n = nullptr;
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->n_scenes = cfg->n_scenes;
+    c->scene_n.resize(c->n_scenes);
+    c->brick_base.resize(c->n_scenes + 1);
+    long long bricks = 0;
+    for (int s = 0; s < c->n_scenes; ++s) {
+        const int n = cfg->scene_grid_n ? cfg->scene_grid_n[s] : cfg->grid_n;
+        if (n < 8 || n > 1024 || n % 4 != 0 || 2 * cfg->bound >= n) { delete c; return MPM_ERR_INVALID_ARGUMENT; }
+        c->scene_n[s] = n;
+        c->brick_base[s] = (int)bricks;
+        bricks += (long long)(n / 4) * (n / 4) * (n / 4);
+    }
+    if (bricks * 64 >= ((long long)1 << 31)) { delete c; return MPM_ERR_INVALID_ARGUMENT; }
+    c->brick_base[c->n_scenes] = (int)bricks;
+    c->total_bricks = (int)bricks;
+    c->cap = (int)std::max<int64_t>(cfg->max_particles, 1);
+    c->h_scenes.resize(c->n_scenes);
+    for (int s = 0; s < c->n_scenes; ++s) {
+        SceneDev& d = c->h_scenes[s];
+        memset(&d, 0, sizeof d);
+        d.n = c->scene_n[s];
+        d.nb = d.n / 4;
+        d.brick_base = c->brick_base[s];
+    }
+    c->h_rigids.assign((size_t)c->n_scenes * kMaxRigids, RigidDev{});
+    c->rigid_type.assign((size_t)c->n_scenes * kMaxRigids, MPM_RIGID_NONE);
+    for (auto& r : c->h_rigids) r.type = MPM_RIGID_NONE;
+
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    const size_t nbk = (size_t)c->total_bricks;
+    c->n_tiles_max = (int)((nbk + kScanTile - 1) / kScanTile);
+    auto alloc = [&](void** p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes ? bytes : 16);
+    };
+    for (int i = 0; i < 2; ++i) alloc((void**)&c->state_mem[i], state_bytes(c->cap));
+    alloc((void**)&c->sb.key, sizeof(int) * c->cap);
+    alloc((void**)&c->sb.rank, sizeof(int) * c->cap);
+    alloc((void**)&c->sb.perm, sizeof(int) * c->cap);
+    alloc((void**)&c->sb.cnt, sizeof(int) * nbk);
+    alloc((void**)&c->sb.off, sizeof(int) * nbk);
+    alloc((void**)&c->sb.act_brick, sizeof(int) * nbk);
+    alloc((void**)&c->sb.act_start, sizeof(int) * nbk);
+    alloc((void**)&c->sb.act_count, sizeof(int) * nbk);
+    alloc((void**)&c->sb.act_scene, sizeof(int) * nbk);
+    alloc((void**)&c->sb.nact_brick, sizeof(int) * nbk);
+    alloc((void**)&c->sb.nact_scene, sizeof(int) * nbk);
+    alloc((void**)&c->sb.counters, sizeof(int) * CTR_COUNT);
+    alloc((void**)&c->sb.tile_status, sizeof(unsigned) * c->n_tiles_max);
+    alloc((void**)&c->sb.tile_agg, sizeof(int4) * c->n_tiles_max);
+    alloc((void**)&c->sb.tile_incl, sizeof(int4) * c->n_tiles_max);
+    alloc((void**)&c->G, sizeof(float4) * nbk * 64);
+    alloc((void**)&c->V, sizeof(float4) * nbk * 64);
+    alloc((void**)&c->brick_epoch, sizeof(int) * nbk);
+    alloc((void**)&c->d_scenes, sizeof(SceneDev) * c->n_scenes);
+    alloc((void**)&c->d_rigids, sizeof(RigidDev) * c->n_scenes * kMaxRigids);
+    alloc((void**)&c->d_impulse, sizeof(double) * c->n_scenes * kMaxRigids * 6);
+    alloc((void**)&c->d_err, sizeof(unsigned) * c->n_scenes);
+    alloc((void**)&c->d_time, sizeof(double) * c->n_scenes);
+    alloc((void**)&c->d_epoch, sizeof(int) * c->n_scenes);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) {
+        for (int i = 0; i < 2; ++i) c->st[i] = state_view(c->state_mem[i], c->cap);
+        cudaMemsetAsync(c->sb.cnt, 0, sizeof(int) * nbk, c->stream);
+        cudaMemsetAsync(c->sb.counters, 0, sizeof(int) * CTR_COUNT, c->stream);
+        cudaMemsetAsync(c->sb.tile_status, 0, sizeof(unsigned) * c->n_tiles_max, c->stream);
+        cudaMemsetAsync(c->G, 0, sizeof(float4) * nbk * 64, c->stream);
+        cudaMemsetAsync(c->V, 0, sizeof(float4) * nbk * 64, c->stream);
+        cudaMemsetAsync(c->brick_epoch, 0xff, sizeof(int) * nbk, c->stream);
+        cudaMemsetAsync(c->d_impulse, 0, sizeof(double) * c->n_scenes * kMaxRigids * 6, c->stream);
+        cudaMemsetAsync(c->d_err, 0, sizeof(unsigned) * c->n_scenes, c->stream);
+        cudaMemsetAsync(c->d_time, 0, sizeof(double) * c->n_scenes, c->stream);
+        cudaMemsetAsync(c->d_epoch, 0, sizeof(int) * c->n_scenes, c->stream);
+        e = cudaMemcpyAsync(c->d_rigids, c->h_rigids.data(), sizeof(RigidDev) * c->h_rigids.size(),
+                            cudaMemcpyHostToDevice, c->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        free_ctx(c);
+        return status_from_cuda(e);
+    }
+    *out = c;
+    return MPM_OK;
+}
+
+extern "C" int mpm_destroy(mpm_ctx* c)
+{
+    free_ctx(c);
+    return MPM_OK;
+}
+
+extern "C" int mpm_set_option(mpm_ctx* c, int option, int64_t value)
+{
+    if (!c) return MPM_ERR_INVALID_ARGUMENT;
+    switch (option) {
+    case MPM_OPT_USE_GRAPHS: c->use_graphs = value != 0; break;
+    case MPM_OPT_LAUNCH_MODE:
+        if (value != 0 && value != 1) return MPM_ERR_INVALID_ARGUMENT;
+        c->launch_mode = (int)value;
+        break;
+    case MPM_OPT_P2G_THREADS:
+    case MPM_OPT_G2P_THREADS:
+        if (value != 128 && value != 256 && value != 512) return MPM_ERR_INVALID_ARGUMENT;
+        (option == MPM_OPT_P2G_THREADS ? c->p2g_threads : c->g2p_threads) = (int)value;
+        break;
+    case MPM_OPT_CTAS_PER_SM:
+        if (value < 0 || value > 32) return MPM_ERR_INVALID_ARGUMENT;
+        c->ctas_per_sm = (int)value;
+        break;
+    case MPM_OPT_GRAPH_CHUNK:
+        if (value < 1 || value > 64) return MPM_ERR_INVALID_ARGUMENT;
+        c->graph_chunk = (int)value;
+        break;
+    case MPM_OPT_PHASE_TIMING: c->phase_timing = value != 0; break;
+    default: return MPM_ERR_INVALID_ARGUMENT;
+    }
+    clear_graphs(c);
+    return MPM_OK;
+}
+
+extern "C" int mpm_scene_count(mpm_ctx* c, int scene, int64_t* count)
+{
+    if (!c || !count || scene < 0 || scene >= c->n_scenes) return MPM_ERR_INVALID_ARGUMENT;
+    *count = c->h_scenes[scene].p_count;
+    return MPM_OK;
+}
+
+// Copy a caller buffer of `bytes` to device memory (returns a device pointer).
+static int stage_input(mpm_ctx* c, const void* src, size_t bytes, int mem, size_t stage_off, const void** dev)
+{
+    if (!src) { *dev = nullptr; return MPM_OK; }
+    if (mem == MPM_MEM_DEVICE) { *dev = src; return MPM_OK; }
+    char* dst = static_cast<char*>(c->d_stage) + stage_off;
+    MPM_CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream));
+    *dev = dst;
+    return MPM_OK;
+}
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+extern "C" int mpm_add_particles(mpm_ctx* c, int scene, int64_t n, const float* x, const float* v, const float* E,
+                                 const float* nu, float E0, float nu0, float rho, float V0, int mem,
+                                 int64_t* first_id_out)
+{
+    if (!c || scene < 0 || scene >= c->n_scenes || n < 0 || (n > 0 && !x)) return MPM_ERR_INVALID_ARGUMENT;
+    if (mem != MPM_MEM_HOST && mem != MPM_MEM_DEVICE) return MPM_ERR_INVALID_ARGUMENT;
+    if (!(rho > 0.f) || !(V0 > 0.f)) return MPM_ERR_INVALID_ARGUMENT;
+    if (!E && !(E0 >= 0.f)) return MPM_ERR_INVALID_ARGUMENT;
+    if (!nu && !(nu0 > -1.f && nu0 < 0.5f)) return MPM_ERR_INVALID_ARGUMENT;
+    if ((int64_t)c->total_particles + n > c->cap) return MPM_ERR_CAPACITY;
+    SceneDev& sc = c->h_scenes[scene];
+    const float m_p = rho * V0;
+    if (sc.p_count > 0 && (sc.m_p != m_p || sc.V0 != V0)) return MPM_ERR_INVALID_ARGUMENT;
+    if (first_id_out) *first_id_out = sc.p_count;
+    if (n == 0) return MPM_OK;
+    if (c->recording) return MPM_ERR_STATE;
+
+    const size_t bx = align256(sizeof(float) * 3 * n), bs = align256(sizeof(float) * n);
+    int st = ensure_stage(c, 2 * bx + 2 * bs);
+    if (st) return st;
+    const void *dx = nullptr, *dv = nullptr, *dE = nullptr, *dnu = nullptr;
+    if ((st = stage_input(c, x, sizeof(float) * 3 * n, mem, 0, &dx))) return st;
+    if ((st = stage_input(c, v, sizeof(float) * 3 * n, mem, bx, &dv))) return st;
+    if ((st = stage_input(c, E, sizeof(float) * n, mem, 2 * bx, &dE))) return st;
+    if ((st = stage_input(c, nu, sizeof(float) * n, mem, 2 * bx + bs, &dnu))) return st;
+
+    // material: uniform unless the scene ever sees per-particle values or a second (E0, nu0)
+    const float mu0 = E0 / (2.f * (1.f + nu0)), lam0 = E0 * nu0 / ((1.f + nu0) * (1.f - 2.f * nu0));
+    bool pp = E || nu || (sc.p_count > 0 && (sc.mu != mu0 || sc.lam != lam0));
+    const int p_at = sc.p_begin + sc.p_count;
+    const int tail = c->total_particles - p_at;
+    PState cur = c->st[c->cur];
+    if (tail > 0) {
+        // make room: copy into the spare buffer with the later scenes shifted by n
+        PState nxt = c->st[c->cur ^ 1];
+        float* arr_src[27] = {};
+        float* arr_dst[27] = {};
+        for (int k = 0; k < 26; ++k) {
+            arr_src[k] = cur.x + (size_t)k * c->cap;
+            arr_dst[k] = nxt.x + (size_t)k * c->cap;
+        }
+        arr_src[26] = reinterpret_cast<float*>(cur.id);
+        arr_dst[26] = reinterpret_cast<float*>(nxt.id);
+        for (int k = 0; k < 27; ++k) {
+            if (p_at > 0)
+                MPM_CK(cudaMemcpyAsync(arr_dst[k], arr_src[k], sizeof(float) * p_at, cudaMemcpyDeviceToDevice, c->stream));
+            MPM_CK(cudaMemcpyAsync(arr_dst[k] + p_at + n, arr_src[k] + p_at, sizeof(float) * tail,
+                                   cudaMemcpyDeviceToDevice, c->stream));
+        }
+        c->cur ^= 1;
+        cur = nxt;
+    }
+    MPM_CK(launch_init_particles(cur, c->cap, p_at, (int)n, sc.p_count, static_cast<const float*>(dx),
+                                 static_cast<const float*>(dv), static_cast<const float*>(dE),
+                                 static_cast<const float*>(dnu), E0, nu0, c->stream));
+    if (pp && !sc.pp_mat && sc.p_count > 0) {
+        // per-particle arrays of the existing particles were not carried: refill them
+        std::vector<float> mu(sc.p_count, sc.mu), lam(sc.p_count, sc.lam);
+        MPM_CK(cudaMemcpyAsync(cur.mu + sc.p_begin, mu.data(), sizeof(float) * sc.p_count, cudaMemcpyHostToDevice, c->stream));
+        MPM_CK(cudaMemcpyAsync(cur.lam + sc.p_begin, lam.data(), sizeof(float) * sc.p_count, cudaMemcpyHostToDevice, c->stream));
+    }
+    if (sc.p_count == 0) {
+        sc.m_p = m_p;
+        sc.V0 = V0;
+        sc.mu = mu0;
+        sc.lam = lam0;
+    }
+    sc.pp_mat = sc.pp_mat || pp;
+    sc.p_count += (int)n;
+    for (int s = scene + 1; s < c->n_scenes; ++s) c->h_scenes[s].p_begin += (int)n;
+    c->total_particles += (int)n;
+    c->scenes_dirty = true;
+    c->keys_valid = false;
+    clear_graphs(c);
+    st = upload_scenes(c);
+    if (st) return st;
+    if (mem == MPM_MEM_HOST) {
+        // the caller may reuse its buffers once we return (pageable copies are staged by
+        // the runtime; wait for the stream so pinned sources are consumed too)
+        st = wait_stream(c);
+        if (st) return st;
+    }
+    return MPM_OK;
+}
+
+extern "C" int mpm_set_rigid(mpm_ctx* c, int scene, int rigid_id, const mpm_rigid* r)
+{
+    if (!c || !r || scene < 0 || scene >= c->n_scenes || rigid_id < 0 || rigid_id >= kMaxRigids) return MPM_ERR_INVALID_ARGUMENT;
+    const int slot = scene * kMaxRigids + rigid_id;
+    RigidDev d{};
+    if (r->type == MPM_RIGID_NONE) {
+        d.type = MPM_RIGID_NONE;
+    } else {
+        if (r->type < MPM_SPHERE || r->type > MPM_SEGMENTS) return MPM_ERR_INVALID_ARGUMENT;
+        if (r->type == MPM_SEGMENTS && (r->n_points < 2 || r->n_points > MPM_MAX_SEGMENT_POINTS)) return MPM_ERR_INVALID_ARGUMENT;
+        const double qn = std::sqrt((double)r->quat[0] * r->quat[0] + (double)r->quat[1] * r->quat[1] +
+                                    (double)r->quat[2] * r->quat[2] + (double)r->quat[3] * r->quat[3]);
+        if (!(qn > 0.0)) return MPM_ERR_INVALID_ARGUMENT;
+        d.type = r->type;
+        d.n_pts = r->type == MPM_SEGMENTS ? r->n_points : 0;
+        for (int i = 0; i < 3; ++i) {
+            d.c0[i] = r->center[i];
+            d.vel[i] = r->vel[i];
+            d.omega[i] = r->omega[i];
+            d.half[i] = r->half[i];
+        }
+        for (int i = 0; i < 4; ++i) d.q0[i] = (float)(r->quat[i] / qn);
+        d.mu_k = r->mu_k;
+        d.c_d = r->c_d;
+        d.margin = r->margin;
+        d.radius = r->radius;
+        d.thickness = r->thickness;
+        d.spine_radius = r->spine_radius;
+        d.t_set = c->h_time;
+        for (int k = 0; k < 3 * d.n_pts; ++k) d.pts[k] = (&r->points[0][0])[k];
+    }
+    c->h_rigids[slot] = d;
+    c->rigid_type[slot] = d.type;
+    int nr = 0;
+    for (int k = 0; k < kMaxRigids; ++k)
+        if (c->rigid_type[scene * kMaxRigids + k] != MPM_RIGID_NONE) nr = k + 1;
+    if (c->h_scenes[scene].n_rigid != nr) {
+        c->h_scenes[scene].n_rigid = nr;
+        c->scenes_dirty = true;
+    }
+    MPM_CK(cudaMemcpyAsync(c->d_rigids + slot, &c->h_rigids[slot], sizeof(RigidDev), cudaMemcpyHostToDevice, c->stream));
+    int st = upload_scenes(c);
+    if (st) return st;
+    // h_rigids[slot] is the copy source; make sure it is consumed before it can change
+    return wait_stream(c);
+}
+
+static uint32_t float_bits(float f)
+{
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return u;
+}
+
+extern "C" int mpm_substep(mpm_ctx* c, float dt, int n_substeps)
+{
+    if (!c || !(dt > 0.f) || !std::isfinite(dt) || n_substeps < 0) return MPM_ERR_INVALID_ARGUMENT;
+    if (n_substeps == 0) return MPM_OK;
+    int st = upload_scenes(c);
+    if (st) return st;
+    if ((st = ensure_keys(c))) return st;
+    if (c->recording) {
+        for (int k = 0; k < n_substeps; ++k)
+            if ((st = mpm_tape_record_substep(c, dt))) return st;
+        return MPM_OK;
+    }
+    if (!c->use_graphs || c->phase_timing) {
+        for (int k = 0; k < n_substeps; ++k) {
+            if ((st = enqueue_substep(c, dt, c->st[c->cur], c->st[c->cur ^ 1]))) return st;
+            c->cur ^= 1;
+            c->h_time += (double)dt;
+        }
+        return MPM_OK;
+    }
+    int left = n_substeps;
+    while (left > 0) {
+        const int L = left >= c->graph_chunk ? c->graph_chunk : 1;
+        auto key = std::make_tuple(float_bits(dt), L, c->cur);
+        auto it = c->graphs.find(key);
+        if (it == c->graphs.end()) {
+            cudaGraph_t g;
+            MPM_CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+            int cur = c->cur;
+            int err = MPM_OK;
+            for (int k = 0; k < L && !err; ++k) {
+                err = enqueue_substep(c, dt, c->st[cur], c->st[cur ^ 1]);
+                cur ^= 1;
+            }
+            cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
+            if (err) return err;
+            MPM_CK(ce);
+            cudaGraphExec_t ex;
+            ce = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            MPM_CK(ce);
+            it = c->graphs.emplace(key, ex).first;
+        }
+        MPM_CK(cudaGraphLaunch(it->second, c->stream));
+        if (L & 1) c->cur ^= 1;
+        for (int k = 0; k < L; ++k) c->h_time += (double)dt;
+        left -= L;
+    }
+    return MPM_OK;
+}
+
+static int error_status(unsigned bits)
+{
+    if (bits & MPM_EBIT_OUT_OF_DOMAIN) return MPM_ERR_OUT_OF_DOMAIN;
+    if (bits & MPM_EBIT_NONFINITE) return MPM_ERR_NONFINITE;
+    if (bits & MPM_EBIT_INVERTED) return MPM_ERR_INVERTED;
+    if (bits & MPM_EBIT_TIMEOUT) return MPM_ERR_TIMEOUT;
+    return MPM_OK;
+}
+
+extern "C" int mpm_get_error(mpm_ctx* c, int scene, uint32_t* bits)
+{
+    if (!c || !bits || scene < 0 || scene >= c->n_scenes) return MPM_ERR_INVALID_ARGUMENT;
+    int st = ensure_pinned(c, 64);
+    if (st) return st;
+    MPM_CK(cudaMemcpyAsync(c->h_pinned, c->d_err + scene, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    if ((st = wait_stream(c))) return st;
+    *bits = *static_cast<unsigned*>(c->h_pinned);
+    return MPM_OK;
+}
+
+static const int kFieldComps[6] = {3, 3, 9, 9, 1, 0};
+
+extern "C" int mpm_read_state(mpm_ctx* c, int scene, uint32_t fields, void* const* dst, int mem)
+{
+    if (!c || !dst || scene < 0 || scene >= c->n_scenes || (fields & ~63u) || !fields) return MPM_ERR_INVALID_ARGUMENT;
+    if (mem != MPM_MEM_HOST && mem != MPM_MEM_DEVICE) return MPM_ERR_INVALID_ARGUMENT;
+    const SceneDev& sc = c->h_scenes[scene];
+    const int np = sc.p_count;
+    int nf = 0;
+    for (int f = 0; f < 6; ++f)
+        if (fields & (1u << f)) {
+            if (!dst[nf]) return MPM_ERR_INVALID_ARGUMENT;
+            ++nf;
+        }
+    int st;
+    // device staging for host reads that are not pinned
+    size_t stage_need = 0, pin_need = 64;
+    for (int f = 0, k = 0; f < 6; ++f) {
+        if (!(fields & (1u << f))) continue;
+        const size_t bytes = f == 5 ? sizeof(double) * kMaxRigids * 6 : sizeof(float) * kFieldComps[f] * (size_t)np;
+        if (mem == MPM_MEM_HOST) {
+            stage_need += align256(bytes);
+            if (!is_pinned_host(dst[k])) pin_need += align256(bytes);
+        }
+        ++k;
+    }
+    if ((st = ensure_stage(c, stage_need))) return st;
+    if ((st = ensure_pinned(c, pin_need))) return st;
+    size_t soff = 0, poff = 64;
+    struct Pending { void* dst; size_t poff, bytes; };
+    std::vector<Pending> pend;
+    const PState cur = c->st[c->cur];
+    for (int f = 0, k = 0; f < 6; ++f) {
+        if (!(fields & (1u << f))) continue;
+        void* out = dst[k++];
+        const size_t bytes = f == 5 ? sizeof(double) * kMaxRigids * 6 : sizeof(float) * kFieldComps[f] * (size_t)np;
+        void* dev_out = out;
+        if (mem == MPM_MEM_HOST) {
+            dev_out = static_cast<char*>(c->d_stage) + soff;
+            soff += align256(bytes);
+        }
+        if (f == 5) {
+            MPM_CK(cudaMemcpyAsync(dev_out, c->d_impulse + (size_t)scene * kMaxRigids * 6, bytes,
+                                   cudaMemcpyDeviceToDevice, c->stream));
+            MPM_CK(cudaMemsetAsync(c->d_impulse + (size_t)scene * kMaxRigids * 6, 0, bytes, c->stream));
+        } else {
+            MPM_CK(launch_gather_field(cur, c->cap, sc.p_begin, np, f, dev_out, c->stream));
+        }
+        if (mem == MPM_MEM_HOST && bytes) {
+            if (is_pinned_host(out)) {
+                MPM_CK(cudaMemcpyAsync(out, dev_out, bytes, cudaMemcpyDeviceToHost, c->stream));
+            } else {
+                MPM_CK(cudaMemcpyAsync(static_cast<char*>(c->h_pinned) + poff, dev_out, bytes, cudaMemcpyDeviceToHost,
+                                       c->stream));
+                pend.push_back({out, poff, bytes});
+                poff += align256(bytes);
+            }
+        }
+    }
+    MPM_CK(cudaMemcpyAsync(c->h_pinned, c->d_err + scene, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    if ((st = wait_stream(c))) return st;
+    for (auto& p : pend) memcpy(p.dst, static_cast<char*>(c->h_pinned) + p.poff, p.bytes);
+    return error_status(*static_cast<unsigned*>(c->h_pinned));
+}
+
+extern "C" int mpm_write_state(mpm_ctx* c, int scene, uint32_t fields, const void* const* src, int mem)
+{
+    if (!c || !src || scene < 0 || scene >= c->n_scenes || !fields || (fields & ~15u)) return MPM_ERR_INVALID_ARGUMENT;
+    if (mem != MPM_MEM_HOST && mem != MPM_MEM_DEVICE) return MPM_ERR_INVALID_ARGUMENT;
+    if (c->recording) return MPM_ERR_STATE;
+    const SceneDev& sc = c->h_scenes[scene];
+    const int np = sc.p_count;
+    size_t need = 0;
+    for (int f = 0, k = 0; f < 4; ++f)
+        if (fields & (1u << f)) {
+            if (!src[k++]) return MPM_ERR_INVALID_ARGUMENT;
+            need += align256(sizeof(float) * kFieldComps[f] * (size_t)np);
+        }
+    int st = MPM_OK;
+    if (mem == MPM_MEM_HOST && (st = ensure_stage(c, need))) return st;
+    size_t off = 0;
+    const PState cur = c->st[c->cur];
+    for (int f = 0, k = 0; f < 4; ++f) {
+        if (!(fields & (1u << f))) continue;
+        const size_t bytes = sizeof(float) * kFieldComps[f] * (size_t)np;
+        const void* d = nullptr;
+        if ((st = stage_input(c, src[k++], bytes, mem, off, &d))) return st;
+        off += align256(bytes);
+        MPM_CK(launch_scatter_field(cur, c->cap, sc.p_begin, np, f, static_cast<const float*>(d), c->stream));
+    }
+    if (fields & MPM_FIELD_X) c->keys_valid = false;
+    if (mem == MPM_MEM_HOST) return wait_stream(c);
+    return MPM_OK;
+}
+
+extern "C" int mpm_read_grid(mpm_ctx* c, int scene, float* dst, int mem)
+{
+    if (!c || !dst || scene < 0 || scene >= c->n_scenes) return MPM_ERR_INVALID_ARGUMENT;
+    if (mem != MPM_MEM_HOST && mem != MPM_MEM_DEVICE) return MPM_ERR_INVALID_ARGUMENT;
+    const int n = c->scene_n[scene];
+    const size_t bytes = sizeof(float) * 4 * (size_t)n * n * n;
+    int st;
+    float* out = dst;
+    if (mem == MPM_MEM_HOST) {
+        if ((st = ensure_stage(c, bytes))) return st;
+        out = static_cast<float*>(c->d_stage);
+    }
+    MPM_CK(cudaMemsetAsync(out, 0, bytes, c->stream));
+    MPM_CK(launch_read_grid(c->V, c->brick_epoch, c->d_epoch, c->d_scenes, scene, n, c->brick_base[scene], out, c->stream));
+    const bool direct = mem == MPM_MEM_HOST && is_pinned_host(dst);
+    if (mem == MPM_MEM_HOST && !direct && (st = ensure_pinned(c, bytes))) return st;
+    if (mem == MPM_MEM_HOST)
+        MPM_CK(cudaMemcpyAsync(direct ? (void*)dst : c->h_pinned, out, bytes, cudaMemcpyDeviceToHost, c->stream));
+    if ((st = wait_stream(c))) return st;
+    if (mem == MPM_MEM_HOST && !direct) memcpy(dst, c->h_pinned, bytes);
+    return MPM_OK;
+}
+
+extern "C" int mpm_autotune(mpm_ctx* c, float dt, int trial_substeps, float* best_ms_out)
+{
+    if (!c || !(dt > 0.f) || trial_substeps < 1 || trial_substeps > 1000) return MPM_ERR_INVALID_ARGUMENT;
+    if (c->recording) return MPM_ERR_STATE;
+    int st = upload_scenes(c);
+    if (st) return st;
+    if ((st = ensure_keys(c))) return st;
+    // snapshot everything a substep changes
+    const size_t sbytes = state_bytes(c->cap);
+    const size_t nbk = (size_t)c->total_bricks;
+    const size_t total = sbytes + 2 * sizeof(int) * c->cap + sizeof(int) * nbk * 2 +
+                         (sizeof(double) + sizeof(int) + sizeof(unsigned) + sizeof(double) * kMaxRigids * 6) * c->n_scenes;
+    char* snap = nullptr;
+    MPM_CK(cudaMalloc(&snap, total));
+    struct Item { void* live; size_t bytes; };
+    const int cur0 = c->cur;
+    Item items[] = {{c->state_mem[cur0], sbytes}, {c->sb.key, sizeof(int) * c->cap}, {c->sb.rank, sizeof(int) * c->cap},
+                    {c->sb.cnt, sizeof(int) * nbk}, {c->brick_epoch, sizeof(int) * nbk},
+                    {c->d_time, sizeof(double) * c->n_scenes}, {c->d_epoch, sizeof(int) * c->n_scenes},
+                    {c->d_err, sizeof(unsigned) * c->n_scenes},
+                    {c->d_impulse, sizeof(double) * kMaxRigids * 6 * c->n_scenes}};
+    auto copy_all = [&](bool save) -> cudaError_t {
+        size_t off = 0;
+        for (auto& it : items) {
+            cudaError_t e = save ? cudaMemcpyAsync(snap + off, it.live, it.bytes, cudaMemcpyDeviceToDevice, c->stream)
+                                 : cudaMemcpyAsync(it.live, snap + off, it.bytes, cudaMemcpyDeviceToDevice, c->stream);
+            if (e != cudaSuccess) return e;
+            off += it.bytes;
+        }
+        return cudaSuccess;
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = copy_all(true);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    const int saved[3] = {c->p2g_threads, c->g2p_threads, c->ctas_per_sm};
+    int best[3] = {saved[0], saved[1], saved[2]};
+    float best_ms = 3.4e38f;
+    const int threads[3] = {128, 256, 512};
+    const int ctas[3] = {0, 2, 4};
+    for (int a = 0; a < 3 && ce == cudaSuccess && st == MPM_OK; ++a)
+        for (int b = 0; b < 3 && ce == cudaSuccess && st == MPM_OK; ++b)
+            for (int k = 0; k < 3 && ce == cudaSuccess && st == MPM_OK; ++k) {
+                c->p2g_threads = threads[a];
+                c->g2p_threads = threads[b];
+                c->ctas_per_sm = ctas[k];
+                // one untimed warm-up substep, then the timed trial
+                st = enqueue_substep(c, dt, c->st[c->cur], c->st[c->cur ^ 1]);
+                c->cur ^= 1;
+                if (!st) ce = cudaEventRecord(e0, c->stream);
+                for (int s = 0; s < trial_substeps && !st && ce == cudaSuccess; ++s) {
+                    st = enqueue_substep(c, dt, c->st[c->cur], c->st[c->cur ^ 1]);
+                    c->cur ^= 1;
+                }
+                if (!st && ce == cudaSuccess) ce = cudaEventRecord(e1, c->stream);
+                if (!st && ce == cudaSuccess) st = wait_stream(c);
+                float ms = 0.f;
+                if (!st && ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+                ms /= trial_substeps;
+                if (!st && ce == cudaSuccess && ms < best_ms) {
+                    best_ms = ms;
+                    best[0] = threads[a];
+                    best[1] = threads[b];
+                    best[2] = ctas[k];
+                }
+                c->cur = cur0;
+                if (ce == cudaSuccess) ce = copy_all(false);
+            }
+    if (ce == cudaSuccess && st == MPM_OK) st = wait_stream(c);
+    c->cur = cur0;
+    c->p2g_threads = best[0];
+    c->g2p_threads = best[1];
+    c->ctas_per_sm = best[2];
+    clear_graphs(c);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(snap);
+    if (ce != cudaSuccess) return status_from_cuda(ce);
+    if (st) return st;
+    if (best_ms_out) *best_ms_out = best_ms;
+    return MPM_OK;
+}
+
+extern "C" int mpm_phase_stats(mpm_ctx* c, double* ms, int64_t* n_substeps, int64_t* active, int reset)
+{
+    if (!c) return MPM_ERR_INVALID_ARGUMENT;
+    int st = ensure_pinned(c, 64);
+    if (st) return st;
+    MPM_CK(cudaMemcpyAsync(c->h_pinned, c->sb.counters, sizeof(int) * 2, cudaMemcpyDeviceToHost, c->stream));
+    if ((st = wait_stream(c))) return st;
+    double sum[4] = {0, 0, 0, 0};
+    for (size_t k = 0; k + 5 <= c->phase_used; k += 5)
+        for (int p = 0; p < 4; ++p) {
+            float t = 0.f;
+            MPM_CK(cudaEventElapsedTime(&t, c->phase_events[k + p], c->phase_events[k + p + 1]));
+            sum[p] += t;
+        }
+    if (ms)
+        for (int p = 0; p < 4; ++p) ms[p] = sum[p];
+    if (n_substeps) *n_substeps = (int64_t)(c->phase_used / 5);
+    if (active) {
+        active[0] = static_cast<int*>(c->h_pinned)[0];
+        active[1] = static_cast<int*>(c->h_pinned)[1];
+    }
+    if (reset) c->phase_used = 0;
+    return MPM_OK;
+}

@@ -1,0 +1,299 @@
+// Device-side data layout and math of the MLS-MPM substep (arXiv 2502.18437,
+// Sec. III-B, Algorithm 1) for sm_103a.
+//
+// Layout in HBM
+//  - particles: structure of arrays, component-major: x[3][cap], v[3][cap],
+//    C[9][cap], F[9][cap], mu[cap], lam[cap], id[cap].  Two copies ping-pong:
+//    each substep reads one through the sort permutation and G2P writes the
+//    other in sorted order, so particles stay sorted by brick in storage.
+//  - grid: each scene owns a dense block of (n/4)^3 bricks of 4^3 nodes;
+//    brick (bx,by,bz) of scene s is global brick brick_base[s] +
+//    (bx*nb + by)*nb + bz and node (lx,ly,lz) of a brick is at
+//    brick*64 + lx*16 + ly*4 + lz.  P2G accumulates float4 (m, mv) per node;
+//    the grid update writes float4 (v, m) to a second array.  Only bricks
+//    touched by particles are ever processed.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mpm.h"
+
+namespace mpm {
+
+constexpr int kMaxRigids = MPM_MAX_RIGIDS;
+constexpr int kMaxPts = MPM_MAX_SEGMENT_POINTS;
+constexpr int kWin = 6;                    // P2G/G2P node window per brick: 4 + 2
+constexpr int kWinNodes = kWin * kWin * kWin;
+
+struct SceneDev {
+    int n;           // nodes per dimension
+    int nb;          // bricks per dimension
+    int brick_base;  // first global brick of the scene
+    int p_begin;     // first particle (storage index)
+    int p_count;     // number of particles
+    int pp_mat;      // 1: per-particle mu/lam arrays
+    int n_rigid;     // rigid slots in use
+    int pad_;
+    float m_p, V0;   // particle mass and initial volume
+    float mu, lam;   // uniform Lame parameters (pp_mat == 0)
+};
+
+struct RigidDev {
+    int type, n_pts;
+    float c0[3], q0[4], vel[3], omega[3];
+    float mu_k, c_d, margin, radius;
+    float half[3];
+    float thickness, spine_radius;
+    double t_set;    // scene time at which (c0, q0) was the pose
+    float pts[kMaxPts * 3];
+};
+
+// Pose of a rigid at the current scene time, staged in shared memory.
+struct RigidCur {
+    int type, n_pts;
+    float c[3], R[9], vel[3], omega[3];
+    float mu_k, c_d, margin, radius;
+    float half[3];
+    float thickness, spine_radius;
+    float pts[kMaxPts * 3];
+};
+
+struct PState {
+    float* x;
+    float* v;
+    float* C;
+    float* F;
+    float* mu;
+    float* lam;
+    int* id;
+};
+
+// Counters shared by the kernels of one substep.
+enum {
+    CTR_N_ACT = 0,     // active particle bricks
+    CTR_N_NACT = 1,    // active node bricks
+    CTR_TICKET = 2,    // scan tile ticket
+    CTR_WORK_P2G = 3,  // dynamic work counters of the persistent kernels
+    CTR_WORK_GRID = 4,
+    CTR_WORK_G2P = 5,
+    CTR_COUNT = 8
+};
+
+// ----------------------------------------------------------------- helpers
+
+__device__ __forceinline__ float3 f3(float a, float b, float c) { return make_float3(a, b, c); }
+
+// Base cell of a coordinate: floor(x*n - 0.5) with one rounding, clamped to
+// [0, n-3] so that the 3-node stencil stays on the grid (NaN maps to 0).
+// Returns 1 when clamping was needed (particle outside the grid).
+__device__ __forceinline__ int base_cell(float x, int n, int& b)
+{
+    float s = floorf(__fmaf_rn(x, (float)n, -0.5f));
+    if (!(s >= 0.0f)) { b = 0; return 1; }
+    if (s > (float)(n - 3)) { b = n - 3; return 1; }
+    b = (int)s;
+    return 0;
+}
+
+__device__ __forceinline__ void bspline(float f, float w[3])
+{
+    // quadratic B-spline at distances f, f-1, f-2 (f in [0.5, 1.5))
+    float a = 1.5f - f, b = f - 1.0f, c = f - 0.5f;
+    w[0] = 0.5f * a * a;
+    w[1] = 0.75f - b * b;
+    w[2] = 0.5f * c * c;
+}
+
+__device__ __forceinline__ float det3(const float F[9])
+{
+    return F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+           F[2] * (F[3] * F[7] - F[4] * F[6]);
+}
+
+// ------------------------------------------------------------- 3x3 SVD
+//
+// Rotation-variant SVD F = U diag(s) V^T (det U = det V = +1, s sorted by
+// decreasing magnitude, s[2] < 0 when det F < 0) in FP32, after McAdams et al.
+// 2011 ("Computing the SVD of 3x3 matrices with minimal branching"): cyclic
+// Jacobi eigen-analysis of the symmetric F^T F for V (here with exact Givens
+// angles, 4 sweeps), sorting of the columns of B = F V, and a Givens QR of B
+// for U and s, which recovers small singular values accurately from B rather
+// than from the squared eigenvalues.
+
+__device__ __forceinline__ void jacobi_rot(float& app, float& aqq, float& apq, float& arp, float& arq,
+                                           float& v0p, float& v0q, float& v1p, float& v1q, float& v2p,
+                                           float& v2q)
+{
+    if (apq == 0.0f) return;
+    float theta = (aqq - app) / (2.0f * apq);
+    float t = copysignf(1.0f, theta) / (fabsf(theta) + sqrtf(__fmaf_rn(theta, theta, 1.0f)));
+    float c = rsqrtf(__fmaf_rn(t, t, 1.0f));
+    float s = t * c;
+    app = __fmaf_rn(-t, apq, app);
+    aqq = __fmaf_rn(t, apq, aqq);
+    apq = 0.0f;
+    float rp = c * arp - s * arq, rq = s * arp + c * arq;
+    arp = rp;
+    arq = rq;
+    float a, b;
+    a = v0p; b = v0q; v0p = c * a - s * b; v0q = s * a + c * b;
+    a = v1p; b = v1q; v1p = c * a - s * b; v1q = s * a + c * b;
+    a = v2p; b = v2q; v2p = c * a - s * b; v2q = s * a + c * b;
+}
+
+__device__ __forceinline__ void swap_neg_cols(float M[9], int i, int j)
+{
+    // swap columns i and j and negate the new column j (keeps the determinant)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        float t = M[3 * r + i];
+        M[3 * r + i] = M[3 * r + j];
+        M[3 * r + j] = -t;
+    }
+}
+
+__device__ __forceinline__ void givens_rows(float B[9], float U[9], int i, int k)
+{
+    // rotate rows i,k of B to zero B[k][i]; U accumulates the transpose
+    float a = B[3 * i + i], b = B[3 * k + i];
+    float r2 = __fmaf_rn(a, a, b * b);
+    float c = 1.0f, s = 0.0f;
+    if (r2 > 1e-37f) {
+        float inv = rsqrtf(r2);
+        c = a * inv;
+        s = b * inv;
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        float bi = B[3 * i + j], bk = B[3 * k + j];
+        B[3 * i + j] = c * bi + s * bk;
+        B[3 * k + j] = -s * bi + c * bk;
+        float ui = U[3 * j + i], uk = U[3 * j + k];
+        U[3 * j + i] = c * ui + s * uk;
+        U[3 * j + k] = -s * ui + c * uk;
+    }
+}
+
+__device__ __forceinline__ void svd3(const float F[9], float U[9], float s[3], float V[9])
+{
+    float a00 = F[0] * F[0] + F[3] * F[3] + F[6] * F[6];
+    float a01 = F[0] * F[1] + F[3] * F[4] + F[6] * F[7];
+    float a02 = F[0] * F[2] + F[3] * F[5] + F[6] * F[8];
+    float a11 = F[1] * F[1] + F[4] * F[4] + F[7] * F[7];
+    float a12 = F[1] * F[2] + F[4] * F[5] + F[7] * F[8];
+    float a22 = F[2] * F[2] + F[5] * F[5] + F[8] * F[8];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) V[i] = (i % 4 == 0) ? 1.0f : 0.0f;
+#pragma unroll
+    for (int sweep = 0; sweep < 4; ++sweep) {
+        jacobi_rot(a00, a11, a01, a02, a12, V[0], V[1], V[3], V[4], V[6], V[7]);
+        jacobi_rot(a00, a22, a02, a01, a12, V[0], V[2], V[3], V[5], V[6], V[8]);
+        jacobi_rot(a11, a22, a12, a01, a02, V[1], V[2], V[4], V[5], V[7], V[8]);
+    }
+    float B[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            B[3 * r + c] = F[3 * r] * V[c] + F[3 * r + 1] * V[3 + c] + F[3 * r + 2] * V[6 + c];
+    // sort by decreasing eigenvalue of F^T F
+    if (a00 < a11) { swap_neg_cols(B, 0, 1); swap_neg_cols(V, 0, 1); float t = a00; a00 = a11; a11 = t; }
+    if (a00 < a22) { swap_neg_cols(B, 0, 2); swap_neg_cols(V, 0, 2); float t = a00; a00 = a22; a22 = t; }
+    if (a11 < a22) { swap_neg_cols(B, 1, 2); swap_neg_cols(V, 1, 2); float t = a11; a11 = a22; a22 = t; }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) U[i] = (i % 4 == 0) ? 1.0f : 0.0f;
+    givens_rows(B, U, 0, 1);
+    givens_rows(B, U, 0, 2);
+    givens_rows(B, U, 1, 2);
+    s[0] = B[0];
+    s[1] = B[4];
+    s[2] = B[8];
+}
+
+// R = U V^T
+__device__ __forceinline__ void mul_abt(const float A[9], const float B[9], float out[9])
+{
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            out[3 * r + c] = A[3 * r] * B[3 * c] + A[3 * r + 1] * B[3 * c + 1] + A[3 * r + 2] * B[3 * c + 2];
+}
+
+// ------------------------------------------------------------ stresses
+//
+// Kirchhoff stress tau = J sigma (the paper's Eq. 6 is the Cauchy form; the
+// Kirchhoff form avoids tracking the current volume, V sigma = V0 tau).
+// Returns error bits (MPM_EBIT_INVERTED when the law needs ln J of J <= 0).
+__device__ __forceinline__ unsigned kirchhoff(int model, const float F[9], float mu, float lam, float tau[9])
+{
+    float J = det3(F);
+    if (model == MPM_NEO_HOOKEAN) {
+        // tau = mu (F F^T - I) + lambda ln(J) I
+        unsigned e = 0;
+        float lnJ = 0.0f;
+        if (J > 0.0f) lnJ = logf(J);
+        else e = MPM_EBIT_INVERTED;
+        mul_abt(F, F, tau);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) tau[i] *= mu;
+        float d = __fmaf_rn(lam, lnJ, -mu);
+        tau[0] += d;
+        tau[4] += d;
+        tau[8] += d;
+        return e;
+    }
+    // fixed-corotated: tau = 2 mu (F - R) F^T + lambda (J - 1) J I
+    float U[9], s[3], V[9], R[9], D[9];
+    svd3(F, U, s, V);
+    mul_abt(U, V, R);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) D[i] = F[i] - R[i];
+    mul_abt(D, F, tau);
+    float mu2 = 2.0f * mu;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) tau[i] *= mu2;
+    float d = lam * (J - 1.0f) * J;
+    tau[0] += d;
+    tau[4] += d;
+    tau[8] += d;
+    return 0u;
+}
+
+// Von Mises return mapping on the Hencky strain (elastoplasticity is the
+// paper's future work, Sec. VI; the law is the library's definition): project
+// the deviatoric log-stretch back to 2 mu |dev ln s| = yield.
+__device__ __forceinline__ unsigned von_mises(float F[9], float mu, float yield)
+{
+    float U[9], s[3], V[9];
+    svd3(F, U, s, V);
+    if (!(s[2] > 0.0f)) return MPM_EBIT_INVERTED;
+    float e0 = logf(s[0]), e1 = logf(s[1]), e2 = logf(s[2]);
+    float tr = (e0 + e1 + e2) * (1.0f / 3.0f);
+    float d0 = e0 - tr, d1 = e1 - tr, d2 = e2 - tr;
+    float nrm = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+    float gamma = nrm - yield / (2.0f * mu);
+    if (!(gamma > 0.0f) || nrm == 0.0f) return 0u;
+    float k = gamma / nrm;
+    float x0 = expf(e0 - k * d0), x1 = expf(e1 - k * d1), x2 = expf(e2 - k * d2);
+    float US[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        US[3 * r] = U[3 * r] * x0;
+        US[3 * r + 1] = U[3 * r + 1] * x1;
+        US[3 * r + 2] = U[3 * r + 2] * x2;
+    }
+    mul_abt(US, V, F);
+    return 0u;
+}
+
+// Rotation matrix of the unit quaternion (w, x, y, z).
+__device__ __forceinline__ void quat_to_mat(float w, float x, float y, float z, float R[9])
+{
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z);       R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y);       R[7] = 2.f * (y * z + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+}  // namespace mpm

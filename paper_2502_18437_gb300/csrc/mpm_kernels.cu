@@ -1,0 +1,991 @@
+// Forward substep kernels of the MLS-MPM transfer loop (arXiv 2502.18437,
+// Algorithm 1) for GB300 (sm_103a):
+//   k_scan     brick histogram -> particle offsets, active particle-brick and
+//              node-brick lists (single-pass decoupled look-back scan)
+//   k_scatter  counting-sort scatter: permutation sorted slot -> particle
+//   k_p2g      P2G (Eq. 1, Eq. 8) into a shared-memory 6^3 node window per
+//              brick, flushed to HBM with vector atomics
+//   k_grid     grid update (Eq. 3), rigid contact (Sec. IV, Eq. 11, Eq. 12),
+//              domain walls, reset of the P2G accumulator
+//   k_g2p      G2P (Eq. 4, Eq. 9, Eq. 10) with the 2x2x2-brick velocity halo
+//              staged by bulk-copy TMA, plasticity, next brick key + rank
+#include <cstdio>
+
+#include "mpm_kernels.cuh"
+
+namespace mpm {
+
+// ------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ unsigned smem_u32(const void* p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void red_add_v4(float4* addr, float a, float b, float c, float d)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false when the bound ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity)
+{
+    for (int it = 0; it < (1 << 22); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ----------------------------------------------------------------- scan
+//
+// One tile = 2048 consecutive bricks of the range.  Each brick contributes
+// (particles, is an active particle brick, is an active node brick); a node
+// brick is active when it or one of its 7 lower neighbours (-1 in any subset
+// of the axes) holds particles, since a particle's 3-node stencil reaches at
+// most 2 nodes beyond its base cell, i.e. into the next brick.
+
+__device__ __forceinline__ int4 add4(int4 a, int4 b) { return make_int4(a.x + b.x, a.y + b.y, a.z + b.z, 0); }
+
+__device__ __forceinline__ int4 shfl_up4(int4 v, int d)
+{
+    return make_int4(__shfl_up_sync(kFull, v.x, d), __shfl_up_sync(kFull, v.y, d), __shfl_up_sync(kFull, v.z, d), 0);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan(StepArgs a)
+{
+    __shared__ int4 s_warp[kScanThreads / 32];
+    __shared__ int4 s_prefix;
+    __shared__ int s_tile;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const SortBufs& sb = a.sb;
+    if (tid == 0) s_tile = atomicAdd(&sb.counters[CTR_TICKET], 1);
+    __syncthreads();
+    const int tile = s_tile;
+    const int n_tiles = (a.r.nbr + kScanTile - 1) / kScanTile;
+    if (tile == 0 && tid == 0) {
+        sb.counters[CTR_WORK_P2G] = 0;
+        sb.counters[CTR_WORK_GRID] = 0;
+        sb.counters[CTR_WORK_G2P] = 0;
+    }
+
+    const int first = a.r.bb0 + tile * kScanTile + tid * kScanItems;
+    const int end = a.r.bb0 + a.r.nbr;
+    // scene of the first item
+    int s = a.r.s0;
+    {
+        int lo = a.r.s0, hi = a.r.s1 - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (a.scenes[mid].brick_base <= first) lo = mid;
+            else hi = mid - 1;
+        }
+        s = lo;
+    }
+    int c[kScanItems], sc[kScanItems];
+    unsigned pf = 0, nf = 0;
+    int4 local = make_int4(0, 0, 0, 0);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int b = first + k;
+        c[k] = 0;
+        sc[k] = s;
+        if (b < end) {
+            while (s + 1 < a.r.s1 && b >= a.scenes[s + 1].brick_base) ++s;
+            sc[k] = s;
+            const int nb = a.scenes[s].nb, lb = b - a.scenes[s].brick_base;
+            const int bz = lb % nb, by = (lb / nb) % nb, bx = lb / (nb * nb);
+            c[k] = __ldg(&sb.cnt[b]);
+            bool nact = c[k] > 0;
+#pragma unroll
+            for (int o = 1; o < 8; ++o) {
+                const int ox = o >> 2, oy = (o >> 1) & 1, oz = o & 1;
+                if (bx >= ox && by >= oy && bz >= oz)
+                    nact |= __ldg(&sb.cnt[b - (ox * nb + oy) * nb - oz]) > 0;
+            }
+            if (c[k] > 0) pf |= 1u << k;
+            if (nact) nf |= 1u << k;
+            local.x += c[k];
+        }
+    }
+    local.y = __popc(pf);
+    local.z = __popc(nf);
+    // block exclusive scan of (particles, pbricks, nbricks)
+    int4 incl = local;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int4 t = shfl_up4(incl, d);
+        if (lane >= d) incl = add4(incl, t);
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int4 w = lane < kScanThreads / 32 ? s_warp[lane] : make_int4(0, 0, 0, 0);
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            int4 t = shfl_up4(w, d);
+            if (lane >= d) w = add4(w, t);
+        }
+        if (lane < kScanThreads / 32) s_warp[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    int4 excl = make_int4(incl.x - local.x, incl.y - local.y, incl.z - local.z, 0);
+    if (warp > 0) excl = add4(excl, s_warp[warp - 1]);
+    // decoupled look-back across tiles
+    if (tid == 0) {
+        const int4 agg = s_warp[kScanThreads / 32 - 1];
+        int4 prefix = make_int4(0, 0, 0, 0);
+        if (tile == 0) {
+            sb.tile_incl[0] = agg;
+            __threadfence();
+            st_release(&sb.tile_status[0], 2u);
+        } else {
+            sb.tile_agg[tile] = agg;
+            __threadfence();
+            st_release(&sb.tile_status[tile], 1u);
+            int j = tile - 1;
+            int spins = 0;
+            while (j >= 0) {
+                unsigned st = ld_acquire(&sb.tile_status[j]);
+                if (st == 2u) {
+                    prefix = add4(prefix, __ldcg(&sb.tile_incl[j]));
+                    break;
+                }
+                if (st == 1u) {
+                    prefix = add4(prefix, __ldcg(&sb.tile_agg[j]));
+                    --j;
+                    continue;
+                }
+                if (++spins > (1 << 24)) {  // predecessor never published: give up, flag
+                    atomicOr(&a.err[a.r.s0], MPM_EBIT_TIMEOUT);
+                    break;
+                }
+                __nanosleep(32);
+            }
+            sb.tile_incl[tile] = add4(prefix, agg);
+            __threadfence();
+            st_release(&sb.tile_status[tile], 2u);
+        }
+        s_prefix = prefix;
+        if (tile == n_tiles - 1) {
+            const int4 tot = add4(prefix, agg);
+            sb.counters[CTR_N_ACT] = tot.y;
+            sb.counters[CTR_N_NACT] = tot.z;
+        }
+    }
+    __syncthreads();
+    excl = add4(excl, s_prefix);
+    int po = a.r.p0 + excl.x, pi = excl.y, ni = excl.z;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int b = first + k;
+        if (pf & (1u << k)) {
+            sb.off[b] = po;
+            sb.act_brick[pi] = b;
+            sb.act_start[pi] = po;
+            sb.act_count[pi] = c[k];
+            sb.act_scene[pi] = sc[k];
+            ++pi;
+        }
+        if (nf & (1u << k)) {
+            sb.nact_brick[ni] = b;
+            sb.nact_scene[ni] = sc[k];
+            ++ni;
+        }
+        po += c[k];
+    }
+}
+
+// Counting-sort scatter; also clears the scan's tile state for the next substep.
+__global__ void k_scatter(StepArgs a, int n_tiles)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = a.r.p0 + g;
+    if (g < a.r.np) a.sb.perm[__ldg(&a.sb.off[a.sb.key[i]]) + a.sb.rank[i]] = i;
+    if (g < n_tiles) a.sb.tile_status[g] = 0u;
+    if (g == 0) a.sb.counters[CTR_TICKET] = 0;
+}
+
+// ----------------------------------------------------- brick key + rank
+
+__device__ __forceinline__ int brick_key(const SceneDev& sc, float x0, float x1, float x2, unsigned& ood)
+{
+    int c0, c1, c2;
+    ood |= (unsigned)(base_cell(x0, sc.n, c0) | base_cell(x1, sc.n, c1) | base_cell(x2, sc.n, c2));
+    return sc.brick_base + ((c0 >> 2) * sc.nb + (c1 >> 2)) * sc.nb + (c2 >> 2);
+}
+
+// Warp-aggregated rank: lanes with the same key get consecutive ranks from one
+// atomic.  Must be called by all 32 lanes; `valid` marks lanes with a particle.
+__device__ __forceinline__ int aggregated_rank(int* cnt, int key, bool valid)
+{
+    const unsigned active = __ballot_sync(kFull, valid);
+    int rank = 0;
+    const unsigned peers = __match_any_sync(kFull, valid ? key : -1) & active;
+    if (valid) {
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&cnt[key], __popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        rank = base + __popc(peers & ((1u << lane) - 1u));
+    }
+    return rank;
+}
+
+__global__ void k_init_keys(StepArgs a, PState st)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = a.r.p0 + g;
+    const bool valid = g < a.r.np;
+    int key = 0, scene = -1;
+    unsigned ood = 0;
+    if (valid) {
+        int lo = a.r.s0, hi = a.r.s1 - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (a.scenes[mid].p_begin <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        // skip empty scenes sharing the same p_begin
+        while (lo + 1 < a.r.s1 && a.scenes[lo].p_count == 0 && a.scenes[lo + 1].p_begin <= i) ++lo;
+        scene = lo;
+        const SceneDev sc = a.scenes[scene];
+        key = brick_key(sc, st.x[i], st.x[a.cap + i], st.x[2 * a.cap + i], ood);
+    }
+    const int rank = aggregated_rank(a.sb.cnt, key, valid);
+    if (valid) {
+        a.sb.key[i] = key;
+        a.sb.rank[i] = rank;
+        if (ood) atomicOr(&a.err[scene], MPM_EBIT_OUT_OF_DOMAIN);
+    }
+}
+
+// ------------------------------------------------------------------ P2G
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_p2g(StepArgs a)
+{
+    __shared__ float sm[4][kWinNodes];
+    __shared__ int s_item;
+    const int tid = threadIdx.x;
+    const int n_act = a.sb.counters[CTR_N_ACT];
+    const int cap = a.cap;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(&a.sb.counters[CTR_WORK_P2G], 1);
+        for (int t = tid; t < 4 * kWinNodes; t += BLOCK) (&sm[0][0])[t] = 0.0f;
+        __syncthreads();
+        const int item = s_item;
+        if (item >= n_act) break;
+        const int b = a.sb.act_brick[item], start = a.sb.act_start[item], count = a.sb.act_count[item];
+        const int scene = a.sb.act_scene[item];
+        if (tid == 0) a.sb.cnt[b] = 0;  // histogram of the next substep starts from zero
+        const SceneDev sc = a.scenes[scene];
+        const int n = sc.n, nb = sc.nb, lb = b - sc.brick_base;
+        const int ox = (lb / (nb * nb)) * 4, oy = ((lb / nb) % nb) * 4, oz = (lb % nb) * 4;
+        const float fn = (float)n, dxs = 1.0f / fn;
+        const float m = sc.m_p;
+        const float kA = a.dt * sc.V0 * 4.0f * fn * fn;  // dt V0 M^-1, M^-1 = 4/dx^2 (Eq. 7)
+        unsigned ebits = 0;
+        for (int k = tid; k < count; k += BLOCK) {
+            const int p = a.sb.perm[start + k];
+            const float x0 = a.in.x[p], x1 = a.in.x[cap + p], x2 = a.in.x[2 * cap + p];
+            float v[3] = {a.in.v[p], a.in.v[cap + p], a.in.v[2 * cap + p]};
+            float C[9], F[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) C[i] = a.in.C[i * cap + p];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) F[i] = a.in.F[i * cap + p];
+            const float mu = sc.pp_mat ? a.in.mu[p] : sc.mu;
+            const float lam = sc.pp_mat ? a.in.lam[p] : sc.lam;
+            int b0, b1, b2;
+            ebits |= (base_cell(x0, n, b0) | base_cell(x1, n, b1) | base_cell(x2, n, b2)) ? MPM_EBIT_OUT_OF_DOMAIN : 0u;
+            const float f0 = __fmaf_rn(x0, fn, -(float)b0);
+            const float f1 = __fmaf_rn(x1, fn, -(float)b1);
+            const float f2 = __fmaf_rn(x2, fn, -(float)b2);
+            float w0[3], w1[3], w2[3];
+            bspline(f0, w0);
+            bspline(f1, w1);
+            bspline(f2, w2);
+            float tau[9];
+            ebits |= kirchhoff(a.model, F, mu, lam, tau);
+            // A = m C - dt V0 M^-1 tau, scaled by dx so that x_I - x_p = ((i,j,k) - f) dx
+            float Ad[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) Ad[i] = (m * C[i] - kA * tau[i]) * dxs;
+            // per node momentum = W (m v + Ad ((i,j,k) - f)) = W (q + i Ad_0 + j Ad_1 + k Ad_2)
+            float q[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) q[r] = m * v[r] - (Ad[3 * r] * f0 + Ad[3 * r + 1] * f1 + Ad[3 * r + 2] * f2);
+            int l0 = b0 - ox, l1 = b1 - oy, l2 = b2 - oz;
+            l0 = min(max(l0, 0), 3);
+            l1 = min(max(l1, 0), 3);
+            l2 = min(max(l2, 0), 3);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const float wij = w0[i] * w1[j];
+                    const float ri0 = q[0] + Ad[0] * i + Ad[1] * j;
+                    const float ri1 = q[1] + Ad[3] * i + Ad[4] * j;
+                    const float ri2 = q[2] + Ad[6] * i + Ad[7] * j;
+                    const int row = (l0 + i) * 36 + (l1 + j) * 6 + l2;
+#pragma unroll
+                    for (int k2 = 0; k2 < 3; ++k2) {
+                        const float W = wij * w2[k2];
+                        const int node = row + k2;
+                        atomicAdd(&sm[0][node], W * m);
+                        atomicAdd(&sm[1][node], W * (ri0 + Ad[2] * k2));
+                        atomicAdd(&sm[2][node], W * (ri1 + Ad[5] * k2));
+                        atomicAdd(&sm[3][node], W * (ri2 + Ad[8] * k2));
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        for (int t = tid; t < kWinNodes; t += BLOCK) {
+            const float mm = sm[0][t];
+            if (mm == 0.0f) continue;
+            const int gi = ox + t / 36, gj = oy + (t / 6) % 6, gk = oz + t % 6;
+            if (gi >= n || gj >= n || gk >= n) continue;
+            const int brick = sc.brick_base + ((gi >> 2) * nb + (gj >> 2)) * nb + (gk >> 2);
+            red_add_v4(&a.G[brick * 64 + (gi & 3) * 16 + (gj & 3) * 4 + (gk & 3)], mm, sm[1][t], sm[2][t], sm[3][t]);
+        }
+        if (ebits) atomicOr(&a.err[scene], ebits);
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------- grid update
+
+// Region test of one rigid at world point x (Sec. IV).  Returns 0 none,
+// 1 regular, 2 one-dimensional (segments), 3 sticky (slicer spine); n is the
+// contact normal (zero when undefined) and t the 1D tangent.
+__device__ int rigid_region(const RigidCur& R, float3 x, float3& n, float3& t)
+{
+    const float dx0 = x.x - R.c[0], dx1 = x.y - R.c[1], dx2 = x.z - R.c[2];
+    // body coordinates p = R^T (x - c)
+    const float p0 = R.R[0] * dx0 + R.R[3] * dx1 + R.R[6] * dx2;
+    const float p1 = R.R[1] * dx0 + R.R[4] * dx1 + R.R[7] * dx2;
+    const float p2 = R.R[2] * dx0 + R.R[5] * dx1 + R.R[8] * dx2;
+    float nl0 = 0.f, nl1 = 0.f, nl2 = 0.f, tl0 = 0.f, tl1 = 0.f, tl2 = 0.f;
+    int code = 0;
+    if (R.type == MPM_SPHERE) {
+        const float l = sqrtf(p0 * p0 + p1 * p1 + p2 * p2);
+        if (l - R.radius < R.margin) {
+            code = 1;
+            if (l > 0.f) { nl0 = p0 / l; nl1 = p1 / l; nl2 = p2 / l; }
+            else nl1 = 1.f;
+        }
+    } else if (R.type == MPM_BOX) {
+        const float q0 = fabsf(p0) - R.half[0], q1 = fabsf(p1) - R.half[1], q2 = fabsf(p2) - R.half[2];
+        const float o0 = fmaxf(q0, 0.f), o1 = fmaxf(q1, 0.f), o2 = fmaxf(q2, 0.f);
+        const float out = sqrtf(o0 * o0 + o1 * o1 + o2 * o2);
+        const float mx = fmaxf(q0, fmaxf(q1, q2));
+        const float sdf = out + fminf(mx, 0.f);
+        if (sdf < R.margin) {
+            code = 1;
+            if (out > 0.f) {
+                nl0 = copysignf(o0 / out, p0);
+                nl1 = copysignf(o1 / out, p1);
+                nl2 = copysignf(o2 / out, p2);
+                // copysignf(0, negative) gives -0: harmless
+            } else if (q0 >= q1 && q0 >= q2) nl0 = p0 >= 0.f ? 1.f : -1.f;
+            else if (q1 >= q2) nl1 = p1 >= 0.f ? 1.f : -1.f;
+            else nl2 = p2 >= 0.f ? 1.f : -1.f;
+        }
+    } else if (R.type == MPM_QUAD_SLICER) {
+        const float A = R.half[0], Bh = R.half[1];
+        const float es = fmaxf(fabsf(p0) - A, 0.f), et = p1 + Bh;
+        const float dsp = sqrtf(es * es + et * et + p2 * p2);
+        if (dsp < R.spine_radius + R.margin) {
+            code = 3;
+        } else {
+            const float qs = fminf(fmaxf(p0, -A), A), qt = fminf(fmaxf(p1, -Bh), Bh);
+            const float d0 = p0 - qs, d1 = p1 - qt, d2 = p2;
+            const float l = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+            if (l < 0.5f * R.thickness + R.margin) {
+                code = 1;
+                if (fabsf(p0) <= A && fabsf(p1) <= Bh) nl2 = p2 >= 0.f ? 1.f : -1.f;
+                else { nl0 = d0 / l; nl1 = d1 / l; nl2 = d2 / l; }
+            }
+        }
+    } else if (R.type == MPM_SEGMENTS) {
+        float best = 3.4e38f, bq0 = 0.f, bq1 = 0.f, bq2 = 0.f;
+        int bs = -1;
+        for (int s = 0; s + 1 < R.n_pts; ++s) {
+            const float a0 = R.pts[3 * s], a1 = R.pts[3 * s + 1], a2 = R.pts[3 * s + 2];
+            const float e0 = R.pts[3 * s + 3] - a0, e1 = R.pts[3 * s + 4] - a1, e2 = R.pts[3 * s + 5] - a2;
+            const float L2 = e0 * e0 + e1 * e1 + e2 * e2;
+            float u = L2 > 0.f ? ((p0 - a0) * e0 + (p1 - a1) * e1 + (p2 - a2) * e2) / L2 : 0.f;
+            u = fminf(fmaxf(u, 0.f), 1.f);
+            const float c0 = a0 + u * e0, c1 = a1 + u * e1, c2 = a2 + u * e2;
+            const float d0 = p0 - c0, d1 = p1 - c1, d2 = p2 - c2;
+            const float l = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+            if (l < best) { best = l; bq0 = c0; bq1 = c1; bq2 = c2; bs = s; }
+        }
+        if (bs >= 0 && best < R.radius + R.margin) {
+            code = 2;
+            if (best > 0.f) { nl0 = (p0 - bq0) / best; nl1 = (p1 - bq1) / best; nl2 = (p2 - bq2) / best; }
+            const float e0 = R.pts[3 * bs + 3] - R.pts[3 * bs], e1 = R.pts[3 * bs + 4] - R.pts[3 * bs + 1],
+                        e2 = R.pts[3 * bs + 5] - R.pts[3 * bs + 2];
+            const float L = sqrtf(e0 * e0 + e1 * e1 + e2 * e2);
+            if (L > 0.f) { tl0 = e0 / L; tl1 = e1 / L; tl2 = e2 / L; }
+        }
+    }
+    n = f3(R.R[0] * nl0 + R.R[1] * nl1 + R.R[2] * nl2, R.R[3] * nl0 + R.R[4] * nl1 + R.R[5] * nl2,
+           R.R[6] * nl0 + R.R[7] * nl1 + R.R[8] * nl2);
+    t = f3(R.R[0] * tl0 + R.R[1] * tl1 + R.R[2] * tl2, R.R[3] * tl0 + R.R[4] * tl1 + R.R[5] * tl2,
+           R.R[6] * tl0 + R.R[7] * tl1 + R.R[8] * tl2);
+    return code;
+}
+
+// Contact correction (Sec. IV-A..C): sticky -> v_rel' = 0; otherwise keep a
+// separating node (v_n >= 0), else v_rel' = c_d max(1 - mu_k |v_n| / |v_t|, 0) v_t
+// with v_t the tangential part (regular) or the part along the 1D tangent.
+// Returns whether the node was changed; dp = node momentum change.
+__device__ bool rigid_contact(const RigidCur& R, float3 x, float m, float3& v, float3& dp)
+{
+    float3 n, t;
+    const int code = rigid_region(R, x, n, t);
+    if (code == 0) return false;
+    const float r0 = x.x - R.c[0], r1 = x.y - R.c[1], r2 = x.z - R.c[2];
+    const float vr0 = R.vel[0] + R.omega[1] * r2 - R.omega[2] * r1;
+    const float vr1 = R.vel[1] + R.omega[2] * r0 - R.omega[0] * r2;
+    const float vr2 = R.vel[2] + R.omega[0] * r1 - R.omega[1] * r0;
+    const float e0 = v.x - vr0, e1 = v.y - vr1, e2 = v.z - vr2;
+    float n0 = 0.f, n1 = 0.f, n2 = 0.f;
+    if (code != 3) {
+        const bool has_n = (n.x * n.x + n.y * n.y + n.z * n.z) > 0.f;
+        float vn = e0 * n.x + e1 * n.y + e2 * n.z;
+        if (has_n && vn >= 0.f) return false;
+        if (!has_n) vn = 0.f;
+        float t0, t1, t2;
+        if (code == 1) {
+            t0 = e0 - vn * n.x; t1 = e1 - vn * n.y; t2 = e2 - vn * n.z;
+        } else {
+            const float a = e0 * t.x + e1 * t.y + e2 * t.z;
+            t0 = a * t.x; t1 = a * t.y; t2 = a * t.z;
+        }
+        const float lt = sqrtf(t0 * t0 + t1 * t1 + t2 * t2);
+        float scale = 0.f;
+        if (lt > 0.f) scale = R.c_d * fmaxf(1.f - R.mu_k * fabsf(vn) / lt, 0.f);
+        n0 = scale * t0; n1 = scale * t1; n2 = scale * t2;
+    }
+    dp = f3(m * (n0 - e0), m * (n1 - e1), m * (n2 - e2));
+    v = f3(vr0 + n0, vr1 + n1, vr2 + n2);
+    return true;
+}
+
+__device__ void stage_rigid(const RigidDev& src, double t_now, RigidCur& dst)
+{
+    const float tau = (float)(t_now - src.t_set);
+    dst.type = src.type;
+    dst.n_pts = src.n_pts;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        dst.c[i] = src.c0[i] + tau * src.vel[i];
+        dst.vel[i] = src.vel[i];
+        dst.omega[i] = src.omega[i];
+        dst.half[i] = src.half[i];
+    }
+    // q(tau) = exp(tau omega / 2) * q0
+    const float wx = src.omega[0], wy = src.omega[1], wz = src.omega[2];
+    const float wn = sqrtf(wx * wx + wy * wy + wz * wz);
+    float qw = src.q0[0], qx = src.q0[1], qy = src.q0[2], qz = src.q0[3];
+    if (wn > 0.f) {
+        float sh, ch;
+        sincosf(0.5f * wn * tau, &sh, &ch);
+        const float ax = wx / wn * sh, ay = wy / wn * sh, az = wz / wn * sh;
+        const float nw = ch * qw - ax * qx - ay * qy - az * qz;
+        const float nx = ch * qx + ax * qw + ay * qz - az * qy;
+        const float ny = ch * qy - ax * qz + ay * qw + az * qx;
+        const float nz = ch * qz + ax * qy - ay * qx + az * qw;
+        qw = nw; qx = nx; qy = ny; qz = nz;
+    }
+    quat_to_mat(qw, qx, qy, qz, dst.R);
+    dst.mu_k = src.mu_k;
+    dst.c_d = src.c_d;
+    dst.margin = src.margin;
+    dst.radius = src.radius;
+    dst.thickness = src.thickness;
+    dst.spine_radius = src.spine_radius;
+}
+
+constexpr int kGridThreads = 64;
+
+__global__ void __launch_bounds__(kGridThreads) k_grid(StepArgs a)
+{
+    __shared__ RigidCur rig[kMaxRigids];
+    __shared__ float simp[kMaxRigids * 6];
+    __shared__ int s_item, s_scene, s_nrig;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int n_nact = a.sb.counters[CTR_N_NACT];
+    if (tid == 0) { s_scene = -1; s_nrig = 0; }
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(&a.sb.counters[CTR_WORK_GRID], 1);
+        __syncthreads();
+        const int item = s_item;
+        const int scene = item < n_nact ? a.sb.nact_scene[item] : -1;
+        if (scene != s_scene) {
+            __syncthreads();
+            if (s_scene >= 0) {
+                for (int t = tid; t < s_nrig * 6; t += kGridThreads)
+                    if (simp[t] != 0.f) atomicAdd(&a.impulse[s_scene * kMaxRigids * 6 + t], (double)simp[t]);
+            }
+            __syncthreads();
+            if (scene >= 0) {
+                const int nr = a.scenes[scene].n_rigid;
+                const double t_now = a.t_scene[scene];
+                if (tid < nr) stage_rigid(a.rigids[scene * kMaxRigids + tid], t_now, rig[tid]);
+                for (int t = tid; t < nr * kMaxPts * 3; t += kGridThreads) {
+                    const int r = t / (kMaxPts * 3), k = t % (kMaxPts * 3);
+                    rig[r].pts[k] = a.rigids[scene * kMaxRigids + r].pts[k];
+                }
+                for (int t = tid; t < kMaxRigids * 6; t += kGridThreads) simp[t] = 0.f;
+                if (tid == 0) { s_nrig = nr; s_scene = scene; }
+            }
+            __syncthreads();
+        }
+        if (item >= n_nact) break;
+        const int B = a.sb.nact_brick[item];
+        const SceneDev sc = a.scenes[scene];
+        const int n = sc.n, nb = sc.nb, lb = B - sc.brick_base;
+        const int gi = (lb / (nb * nb)) * 4 + (tid >> 4);
+        const int gj = ((lb / nb) % nb) * 4 + ((tid >> 2) & 3);
+        const int gk = (lb % nb) * 4 + (tid & 3);
+        const int node = B * 64 + tid;
+        const float4 g = a.G[node];
+        a.G[node] = make_float4(0.f, 0.f, 0.f, 0.f);
+        float3 v = f3(0.f, 0.f, 0.f);
+        const float dxs = 1.0f / (float)n;
+        float dpr[kMaxRigids][3];
+        unsigned touched = 0;
+        const int nr = s_nrig;
+        if (g.x > 0.f) {
+            v = f3(g.y / g.x + a.dt * a.gravity[0], g.z / g.x + a.dt * a.gravity[1], g.w / g.x + a.dt * a.gravity[2]);
+            const float3 xI = f3(gi * dxs, gj * dxs, gk * dxs);
+            for (int r = 0; r < nr; ++r) {
+                float3 dp;
+                if (rigid_contact(rig[r], xI, g.x, v, dp)) {
+                    touched |= 1u << r;
+                    dpr[r][0] = dp.x; dpr[r][1] = dp.y; dpr[r][2] = dp.z;
+                }
+            }
+            const int lo = a.bound, hi = n - 1 - a.bound;
+            if (gi < lo) v.x = fmaxf(v.x, 0.f);
+            if (gi > hi) v.x = fminf(v.x, 0.f);
+            if (gj < lo) {
+                if (a.floor_sticky) v = f3(0.f, 0.f, 0.f);
+                else v.y = fmaxf(v.y, 0.f);
+            }
+            if (gj > hi) v.y = fminf(v.y, 0.f);
+            if (gk < lo) v.z = fmaxf(v.z, 0.f);
+            if (gk > hi) v.z = fminf(v.z, 0.f);
+        }
+        a.V[node] = make_float4(v.x, v.y, v.z, g.x);
+        if (tid == 0) a.brick_epoch[B] = a.epoch[scene];
+        // impulse on each rigid: -(node momentum change), linear and angular
+        for (int r = 0; r < nr; ++r) {
+            const bool on = (touched >> r) & 1u;
+            if (!__any_sync(kFull, on)) continue;
+            float val[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (on) {
+                const float d0 = -dpr[r][0], d1 = -dpr[r][1], d2 = -dpr[r][2];
+                const float r0 = gi * dxs - rig[r].c[0], r1 = gj * dxs - rig[r].c[1], r2 = gk * dxs - rig[r].c[2];
+                val[0] = d0; val[1] = d1; val[2] = d2;
+                val[3] = r1 * d2 - r2 * d1;
+                val[4] = r2 * d0 - r0 * d2;
+                val[5] = r0 * d1 - r1 * d0;
+            }
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                float x = val[c];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+                if (lane == 0) atomicAdd(&simp[r * 6 + c], x);
+            }
+        }
+        __syncthreads();
+    }
+    if (s_scene >= 0) {
+        for (int t = tid; t < s_nrig * 6; t += kGridThreads)
+            if (simp[t] != 0.f) atomicAdd(&a.impulse[s_scene * kMaxRigids * 6 + t], (double)simp[t]);
+    }
+}
+
+// ------------------------------------------------------------------ G2P
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_g2p(StepArgs a)
+{
+    __shared__ __align__(128) float4 vw[8 * 64];
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ int s_item;
+    const int tid = threadIdx.x;
+    const int cap = a.cap;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    if (blockIdx.x == 0) {
+        // scene clocks advance once per substep (read by the next grid update)
+        for (int s = a.r.s0 + tid; s < a.r.s1; s += BLOCK) {
+            a.t_scene[s] += (double)a.dt;
+            a.epoch[s] += 1;
+        }
+    }
+    __syncthreads();
+    unsigned phase = 0;
+    const int n_act = a.sb.counters[CTR_N_ACT];
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(&a.sb.counters[CTR_WORK_G2P], 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= n_act) break;
+        const int b = a.sb.act_brick[item], start = a.sb.act_start[item], count = a.sb.act_count[item];
+        const int scene = a.sb.act_scene[item];
+        const SceneDev sc = a.scenes[scene];
+        const int n = sc.n, nb = sc.nb, lb = b - sc.brick_base;
+        const int bx = lb / (nb * nb), by = (lb / nb) % nb, bz = lb % nb;
+        if (tid == 0) {
+            // stage the 2x2x2 node bricks (b + {0,1}^3) holding the 6^3 window
+            fence_proxy_async();
+            unsigned bytes = 0;
+#pragma unroll
+            for (int o = 0; o < 8; ++o)
+                if (bx + (o >> 2) < nb && by + ((o >> 1) & 1) < nb && bz + (o & 1) < nb) bytes += 64 * sizeof(float4);
+            mbar_expect_tx(&bar, bytes);
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                const int cx = bx + (o >> 2), cy = by + ((o >> 1) & 1), cz = bz + (o & 1);
+                if (cx < nb && cy < nb && cz < nb) {
+                    const int nbk = sc.brick_base + (cx * nb + cy) * nb + cz;
+                    bulk_g2s(&vw[o * 64], &a.V[nbk * 64], 64 * sizeof(float4), &bar);
+                }
+            }
+        }
+        const bool ok = mbar_wait_bounded(&bar, phase);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicOr(&a.err[scene], MPM_EBIT_TIMEOUT);
+            mbar_wait_bounded(&bar, phase);  // let copies in flight land before leaving
+            return;
+        }
+        phase ^= 1u;
+        const float fn = (float)n, dt = a.dt;
+        const int ox = bx * 4, oy = by * 4, oz = bz * 4;
+        unsigned ebits = 0;
+        for (int k0 = 0; k0 < count; k0 += BLOCK) {
+            const int k = k0 + tid;
+            const bool valid = k < count;
+            int key = 0;
+            unsigned ood = 0;
+            float xn[3], vp[3], Cn[9], Fn[9], mu = 0.f, lam = 0.f;
+            int pid = 0;
+            if (valid) {
+                const int p = a.sb.perm[start + k];
+                const float x0 = a.in.x[p], x1 = a.in.x[cap + p], x2 = a.in.x[2 * cap + p];
+                float F[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) F[i] = a.in.F[i * cap + p];
+                pid = a.in.id[p];
+                if (sc.pp_mat) { mu = a.in.mu[p]; lam = a.in.lam[p]; }
+                else { mu = sc.mu; lam = sc.lam; }
+                int b0, b1, b2;
+                base_cell(x0, n, b0);
+                base_cell(x1, n, b1);
+                base_cell(x2, n, b2);
+                const float f0 = __fmaf_rn(x0, fn, -(float)b0);
+                const float f1 = __fmaf_rn(x1, fn, -(float)b1);
+                const float f2 = __fmaf_rn(x2, fn, -(float)b2);
+                float w0[3], w1[3], w2[3];
+                bspline(f0, w0);
+                bspline(f1, w1);
+                bspline(f2, w2);
+                const int l0 = min(max(b0 - ox, 0), 3), l1 = min(max(b1 - oy, 0), 3), l2 = min(max(b2 - oz, 0), 3);
+                float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+                float B[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) B[i] = 0.f;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const int wi = l0 + i;
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        const int wj = l1 + j;
+                        const float wij = w0[i] * w1[j];
+#pragma unroll
+                        for (int k2 = 0; k2 < 3; ++k2) {
+                            const int wk = l2 + k2;
+                            const int sub = ((wi >> 2) << 2) | ((wj >> 2) << 1) | (wk >> 2);
+                            const float4 g = vw[sub * 64 + (wi & 3) * 16 + (wj & 3) * 4 + (wk & 3)];
+                            const float W = wij * w2[k2];
+                            const float g0 = W * g.x, g1 = W * g.y, g2 = W * g.z;
+                            v0 += g0; v1 += g1; v2 += g2;
+                            const float d0 = (float)i - f0, d1 = (float)j - f1, d2 = (float)k2 - f2;
+                            B[0] += g0 * d0; B[1] += g0 * d1; B[2] += g0 * d2;
+                            B[3] += g1 * d0; B[4] += g1 * d1; B[5] += g1 * d2;
+                            B[6] += g2 * d0; B[7] += g2 * d1; B[8] += g2 * d2;
+                        }
+                    }
+                }
+                // C = D^-1 sum N v (x_I - x_p)^T = 4/dx^2 * dx * B  (Eq. 9)
+                const float c4 = 4.0f * fn;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) Cn[i] = c4 * B[i];
+                vp[0] = v0; vp[1] = v1; vp[2] = v2;
+                xn[0] = x0 + dt * v0;
+                xn[1] = x1 + dt * v1;
+                xn[2] = x2 + dt * v2;
+                // F <- (I + dt C) F  (Eq. 10)
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        Fn[3 * r + c] = F[3 * r + c] + dt * (Cn[3 * r] * F[c] + Cn[3 * r + 1] * F[3 + c] + Cn[3 * r + 2] * F[6 + c]);
+                if (a.plasticity) ebits |= von_mises(Fn, mu, a.yield_stress);
+                float chk = xn[0] + xn[1] + xn[2] + v0 + v1 + v2;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) chk += Fn[i];
+                if (!isfinite(chk)) ebits |= MPM_EBIT_NONFINITE;
+                key = brick_key(sc, xn[0], xn[1], xn[2], ood);
+                if (ood) ebits |= MPM_EBIT_OUT_OF_DOMAIN;
+            }
+            const int rank = aggregated_rank(a.sb.cnt, key, valid);
+            if (valid) {
+                const int s = start + k;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    a.out.x[d * cap + s] = xn[d];
+                    a.out.v[d * cap + s] = vp[d];
+                }
+#pragma unroll
+                for (int i = 0; i < 9; ++i) a.out.C[i * cap + s] = Cn[i];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) a.out.F[i * cap + s] = Fn[i];
+                if (sc.pp_mat) { a.out.mu[s] = mu; a.out.lam[s] = lam; }
+                a.out.id[s] = pid;
+                a.sb.key[s] = key;
+                a.sb.rank[s] = rank;
+            }
+        }
+        if (ebits) atomicOr(&a.err[scene], ebits);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------- state I/O kernels
+
+__global__ void k_gather_field(PState st, int cap, int p0, int np, int field, void* dst)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= np) return;
+    const int s = p0 + g;
+    const int id = st.id[s];
+    if (field == 4) { static_cast<int*>(dst)[g] = id; return; }
+    const float* src = field == 0 ? st.x : field == 1 ? st.v : field == 2 ? st.C : st.F;
+    const int comps = field < 2 ? 3 : 9;
+    float* out = static_cast<float*>(dst) + (size_t)id * comps;
+    for (int c = 0; c < comps; ++c) out[c] = src[(size_t)c * cap + s];
+}
+
+__global__ void k_scatter_field(PState st, int cap, int p0, int np, int field, const float* src)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= np) return;
+    const int s = p0 + g;
+    const int id = st.id[s];
+    float* dst = field == 0 ? st.x : field == 1 ? st.v : field == 2 ? st.C : st.F;
+    const int comps = field < 2 ? 3 : 9;
+    const float* in = src + (size_t)id * comps;
+    for (int c = 0; c < comps; ++c) dst[(size_t)c * cap + s] = in[c];
+}
+
+__global__ void k_init_particles(PState st, int cap, int p_at, int n, int id0, const float* x, const float* v,
+                                 const float* E, const float* nu, float E0, float nu0)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const int s = p_at + g;
+    for (int d = 0; d < 3; ++d) {
+        st.x[(size_t)d * cap + s] = x[3 * (size_t)g + d];
+        st.v[(size_t)d * cap + s] = v ? v[3 * (size_t)g + d] : 0.f;
+    }
+    for (int i = 0; i < 9; ++i) {
+        st.C[(size_t)i * cap + s] = 0.f;
+        st.F[(size_t)i * cap + s] = (i % 4 == 0) ? 1.f : 0.f;
+    }
+    const float e = E ? E[g] : E0, q = nu ? nu[g] : nu0;
+    st.mu[s] = e / (2.f * (1.f + q));
+    st.lam[s] = e * q / ((1.f + q) * (1.f - 2.f * q));
+    st.id[s] = id0 + g;
+}
+
+__global__ void k_read_grid(const float4* V, const int* brick_epoch, const int* epoch, int scene, int n,
+                            int brick_base, float* dst)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long total = (long long)n * n * n;
+    if (g >= total) return;
+    const int nb = n / 4;
+    const int brick = (int)(g >> 6), loc = (int)(g & 63);
+    const int B = brick_base + brick;
+    if (brick_epoch[B] != epoch[scene] - 1) return;
+    const int bx = brick / (nb * nb), by = (brick / nb) % nb, bz = brick % nb;
+    const int gi = bx * 4 + (loc >> 4), gj = by * 4 + ((loc >> 2) & 3), gk = bz * 4 + (loc & 3);
+    const float4 v = V[(size_t)B * 64 + loc];
+    float* o = dst + (((size_t)gi * n + gj) * n + gk) * 4;
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+
+// ------------------------------------------------------------- launchers
+
+static int n_blocks(long long n, int t) { return (int)((n + t - 1) / t); }
+
+cudaError_t launch_init_keys(const StepArgs& a, const PState& st, cudaStream_t s)
+{
+    if (a.r.np == 0) return cudaSuccess;
+    k_init_keys<<<n_blocks(a.r.np, 256), 256, 0, s>>>(a, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort(const StepArgs& a, cudaStream_t s)
+{
+    const int n_tiles = (a.r.nbr + kScanTile - 1) / kScanTile;
+    k_scan<<<n_tiles, kScanThreads, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int work = a.r.np > n_tiles ? a.r.np : n_tiles;
+    k_scatter<<<n_blocks(work, 256), 256, 0, s>>>(a, n_tiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_p2g(const StepArgs& a, cudaStream_t s)
+{
+    switch (a.p2g_threads) {
+    case 128: k_p2g<128><<<a.persistent_ctas, 128, 0, s>>>(a); break;
+    case 512: k_p2g<512><<<a.persistent_ctas, 512, 0, s>>>(a); break;
+    default: k_p2g<256><<<a.persistent_ctas, 256, 0, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grid(const StepArgs& a, cudaStream_t s)
+{
+    k_grid<<<a.persistent_ctas * 4, kGridThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_g2p(const StepArgs& a, cudaStream_t s)
+{
+    switch (a.g2p_threads) {
+    case 128: k_g2p<128><<<a.persistent_ctas, 128, 0, s>>>(a); break;
+    case 512: k_g2p<512><<<a.persistent_ctas, 512, 0, s>>>(a); break;
+    default: k_g2p<256><<<a.persistent_ctas, 256, 0, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_field(const PState& st, int cap, int p0, int np, int field, void* dst, cudaStream_t s)
+{
+    if (np == 0) return cudaSuccess;
+    k_gather_field<<<n_blocks(np, 256), 256, 0, s>>>(st, cap, p0, np, field, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_field(const PState& st, int cap, int p0, int np, int field, const float* src, cudaStream_t s)
+{
+    if (np == 0) return cudaSuccess;
+    k_scatter_field<<<n_blocks(np, 256), 256, 0, s>>>(st, cap, p0, np, field, src);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_particles(const PState& st, int cap, int p_at, int n, int id0, const float* x, const float* v,
+                                  const float* E, const float* nu, float E0, float nu0, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_init_particles<<<n_blocks(n, 256), 256, 0, s>>>(st, cap, p_at, n, id0, x, v, E, nu, E0, nu0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_read_grid(const float4* V, const int* brick_epoch, const int* epoch, const SceneDev*, int scene,
+                             int n, int brick_base, float* dst, cudaStream_t s)
+{
+    const long long total = (long long)n * n * n;
+    k_read_grid<<<n_blocks(total, 256), 256, 0, s>>>(V, brick_epoch, epoch, scene, n, brick_base, dst);
+    return cudaGetLastError();
+}
+
+int occupancy_p2g(int threads)
+{
+    int b = 0;
+    if (threads == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_p2g<128>, 128, 0);
+    else if (threads == 512) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_p2g<512>, 512, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_p2g<256>, 256, 0);
+    return b;
+}
+
+int occupancy_g2p(int threads)
+{
+    int b = 0;
+    if (threads == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<128>, 128, 0);
+    else if (threads == 512) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<512>, 512, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<256>, 256, 0);
+    return b;
+}
+
+}  // namespace mpm

@@ -1,0 +1,80 @@
+// Kernel parameter blocks and host-side launchers of the forward substep.
+#pragma once
+
+#include "mpm_device.cuh"
+
+namespace mpm {
+
+struct Range {
+    int s0, s1;     // scene range [s0, s1)
+    int bb0, nbr;   // global brick range [bb0, bb0 + nbr)
+    int p0, np;     // particle range [p0, p0 + np)
+};
+
+struct SortBufs {
+    int* key;       // [cap] brick of each stored particle (next substep)
+    int* rank;      // [cap] rank of the particle within its brick
+    int* perm;      // [cap] sorted slot -> storage index
+    int* cnt;       // [bricks] particles per brick (next substep)
+    int* off;       // [bricks] first slot of each active brick
+    int* act_brick; // [bricks] active particle bricks
+    int* act_start;
+    int* act_count;
+    int* act_scene;
+    int* nact_brick;// [bricks] active node bricks
+    int* nact_scene;
+    int* counters;  // [CTR_COUNT]
+    unsigned* tile_status;
+    int4* tile_agg;
+    int4* tile_incl;
+};
+
+struct StepArgs {
+    Range r;
+    SortBufs sb;
+    const SceneDev* scenes;
+    const RigidDev* rigids;      // [n_scenes * kMaxRigids]
+    double* impulse;             // [n_scenes * kMaxRigids * 6]
+    double* t_scene;             // [n_scenes] scene clocks
+    int* epoch;                  // [n_scenes] substep counters
+    int* brick_epoch;            // [bricks] substep of the last grid update of a node brick
+    unsigned* err;               // [n_scenes]
+    float4* G;                   // P2G accumulator (m, mv)
+    float4* V;                   // node (v, m)
+    PState in, out;
+    int cap;
+    float dt;
+    float gravity[3];
+    int bound, floor_sticky;
+    int model, plasticity;
+    float yield_stress;
+    int persistent_ctas;         // CTAs of the persistent kernels
+    int p2g_threads, g2p_threads;
+};
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+cudaError_t launch_init_keys(const StepArgs& a, const PState& st, cudaStream_t s);
+cudaError_t launch_sort(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_p2g(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_grid(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_g2p(const StepArgs& a, cudaStream_t s);
+
+// state I/O helpers
+cudaError_t launch_gather_field(const PState& st, int cap, int p0, int np, int field, void* dst,
+                                cudaStream_t s);
+cudaError_t launch_init_particles(const PState& st, int cap, int p_at, int n, int id0, const float* x,
+                                  const float* v, const float* E, const float* nu, float E0, float nu0,
+                                  cudaStream_t s);
+cudaError_t launch_permute_to_id(const PState& src, const PState& dst, int cap, int p0, int np,
+                                 cudaStream_t s);
+cudaError_t launch_scatter_field(const PState& st, int cap, int p0, int np, int field, const float* src,
+                                 cudaStream_t s);
+cudaError_t launch_read_grid(const float4* V, const int* brick_epoch, const int* epoch, const SceneDev* scenes,
+                             int scene, int n, int brick_base, float* dst, cudaStream_t s);
+int occupancy_p2g(int threads);
+int occupancy_g2p(int threads);
+
+}  // namespace mpm

@@ -152,14 +152,14 @@ SCALE_POINTS = {65536: 64, 262144: 128, 1048576: 256, 4194304: 256}
 def tissue_block(N=1048576, n=None, seed=2, substeps=500, dt=5e-5, plasticity=True):
     """Scale-sweep block: N uniform points (8 per cell on average) in an
     axis-aligned cube of side (N/8)^(1/3) dx, centred in x and z with its bottom
-    at y = 0.03, falling at 2 m/s onto the sticky floor; fixed-corotated
+    at y = 0.03 (or 4 dx on coarse grids, to start clear of the wall), falling at 2 m/s onto the sticky floor; fixed-corotated
     E = 1e4, nu = 0.3, rho = 1000, von Mises yield 50."""
     if n is None:
         n = SCALE_POINTS.get(N, 256)
     dx = 1.0 / n
     side = (N / 8.0) ** (1.0 / 3.0) * dx
     g = rng(seed + 1000 * (N % 997))
-    lo = np.array([0.5 - side / 2, 0.03, 0.5 - side / 2])
+    lo = np.array([0.5 - side / 2, max(0.03, 4.0 * dx), 0.5 - side / 2])  # clear of the 3-node wall
     x = lo + g.random((N, 3)) * side
     V0 = side ** 3 / N
     v = np.broadcast_to(np.array([0.0, -2.0, 0.0]), (N, 3))

@@ -1,0 +1,175 @@
+"""GPU tests of the C ABI's behaviour: batching, ragged and empty scenes, error
+reporting, state round trips, autotuning.  All through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2502_18437_gb300 import mpm, workloads as W
+from tests.parity_util import assert_close, oracle_cfg, oracle_state
+
+pytestmark = pytest.mark.gpu
+
+
+def small_cube(N_side=6, corner=(0.4, 0.4, 0.4), n=32):
+    sc = W.elastic_cube(n=n, n_side=N_side, corner=corner, substeps=10)
+    return sc
+
+
+def test_batched_scenes_match_single_scene_runs():
+    # Ragged batch: empty scene, one particle, a few, a full cube; two grid sizes.
+    scenes = [small_cube(0), small_cube(1), small_cube(3, (0.2, 0.5, 0.6)), W.elastic_cube(), small_cube(7, n=64)]
+    scenes[0]["rigids"] = []
+    scenes[3]["rigids"] = [W.sphere((0.5, 0.12, 0.5), 0.05, margin=1 / 32)]
+    with mpm.from_scenes(scenes) as sim:
+        sim.substep(1e-4, 15)
+        batched = [sim.read_state(s) for s in range(len(scenes))]
+    for s, sc in enumerate(scenes):
+        assert len(batched[s]["x"]) == len(sc["x"])
+        if len(sc["x"]) == 0:
+            continue
+        with mpm.from_workload(sc) as sim:
+            sim.substep(1e-4, 15)
+            alone = sim.read_state(0)
+        for f in ("x", "v", "C", "F"):
+            assert_close(f"scene {s} {f}", batched[s][f], alone[f], rtol=1e-5, rel_scale=1e-5)
+
+
+def test_batched_looped_mode_matches():
+    scenes = W.batched_scenes(n_scenes=6, substeps=10)
+    res = []
+    for mode in (0, 1):
+        with mpm.from_scenes(scenes) as sim:
+            sim.set_option("launch_mode", mode)
+            sim.substep(1e-4, 10)
+            res.append([sim.read_state(s) for s in range(len(scenes))])
+    for s in range(len(scenes)):
+        for f in ("x", "v"):
+            assert_close(f"scene {s} {f}", res[1][s][f], res[0][s][f], rtol=1e-5, rel_scale=1e-5)
+
+
+def test_single_particle_free_fall_matches_closed_form():
+    sc = small_cube(1, (0.5, 0.5, 0.5))
+    with mpm.from_workload(sc) as sim:
+        sim.substep(1e-3, 10)
+        st = sim.read_state(0)
+    g = -9.8
+    assert abs(st["v"][0, 1] - 10 * 1e-3 * g) < 1e-5
+    assert abs(st["x"][0, 1] - (sc["x"][0, 1] + 1e-6 * g * 55)) < 1e-6
+
+
+def test_empty_context_substeps():
+    with mpm.Simulation(32, 16) as sim:
+        sim.substep(1e-4, 3)
+        out = sim.read_state(0, ("x",))
+        assert out["x"].shape == (0, 3)
+
+
+def test_write_read_roundtrip_and_order():
+    sc = W.elastic_cube(n_side=8)
+    g = np.random.default_rng(0)
+    N = len(sc["x"])
+    with mpm.from_workload(sc) as sim:
+        sim.substep(1e-4, 3)  # storage order is now the sorted order
+        vals = {"x": sc["x"] + 0.001 * g.random((N, 3)).astype(np.float32),
+                "v": g.normal(size=(N, 3)).astype(np.float32),
+                "C": g.normal(size=(N, 3, 3)).astype(np.float32),
+                "F": g.normal(size=(N, 3, 3)).astype(np.float32)}
+        sim.write_state(0, **vals)
+        out = sim.read_state(0)
+        for f, a in vals.items():
+            assert np.array_equal(out[f], a), f
+
+
+def test_device_tensors_roundtrip():
+    torch = pytest.importorskip("torch")
+    sc = W.elastic_cube(n_side=8)
+    with mpm.from_workload(sc) as sim:
+        sim.substep(1e-4, 2)
+        host = sim.read_state(0)
+        dev = sim.read_state(0, device=True)
+        for f in ("x", "v", "C", "F"):
+            assert np.array_equal(dev[f].cpu().numpy(), host[f])
+        sim.write_state(0, v=dev["v"] * 2)
+        assert np.array_equal(sim.read_state(0, ("v",))["v"], 2 * host["v"])
+
+
+def test_out_of_domain_reported():
+    sc = small_cube(2, (0.0, 0.5, 0.5))  # first layer's base cell is -1
+    with mpm.from_workload(sc) as sim:
+        sim.substep(1e-4, 1)
+        out = sim.read_state(0, ("x",), check=False)
+        assert out["status"] == -4
+        assert sim.error_bits(0) & mpm.EBIT["out_of_domain"]
+
+
+def test_nonfinite_reported():
+    sc = small_cube(2)
+    v = sc["v"].copy()
+    v[0, 0] = np.nan
+    with mpm.from_workload(sc) as sim:
+        sim.write_state(0, v=v)
+        sim.substep(1e-4, 1)
+        assert sim.read_state(0, ("x",), check=False)["status"] == -5
+
+
+def test_neo_hookean_inversion_reported():
+    sc = small_cube(2)
+    sc["model"] = "neo_hookean"
+    N = len(sc["x"])
+    F = np.tile(np.diag([1.0, 1.0, -1.0]).astype(np.float32), (N, 1, 1))
+    with mpm.from_workload(sc) as sim:
+        sim.write_state(0, F=F)
+        sim.substep(1e-5, 1)
+        assert sim.read_state(0, ("x",), check=False)["status"] == -6
+
+
+def test_invalid_arguments():
+    with pytest.raises(mpm.MPMError) as e:
+        mpm.Simulation(30, 10)  # n not a multiple of 4
+    assert e.value.status == -1
+    with mpm.Simulation(32, 10) as sim:
+        with pytest.raises(mpm.MPMError) as e:
+            sim.add_particles(0, np.full((11, 3), 0.5, np.float32), E0=1e3, nu0=0.3, rho=1, V0=1e-6)
+        assert e.value.status == -7  # capacity
+        with pytest.raises(mpm.MPMError):
+            sim.add_particles(1, np.full((1, 3), 0.5, np.float32), E0=1e3, nu0=0.3, rho=1, V0=1e-6)
+        with pytest.raises(mpm.MPMError):
+            sim.substep(-1.0, 1)
+        with pytest.raises(mpm.MPMError):
+            sim.set_option("p2g_threads", 100)
+        with pytest.raises(mpm.MPMError) as e:
+            sim.backward()
+        assert e.value.status in (-1, -9)
+
+
+def test_autotune_restores_state():
+    sc = W.tissue_block(N=65536, n=64)
+    with mpm.from_workload(sc) as sim:
+        sim.substep(sc["dt"], 5)
+        before = sim.read_state(0)
+        ms = sim.autotune(sc["dt"], 3)
+        assert ms > 0
+        after = sim.read_state(0)
+        for f in ("x", "v", "C", "F"):
+            assert np.array_equal(before[f], after[f])
+        sim.substep(sc["dt"], 5)
+        tuned = sim.read_state(0)
+    with mpm.from_workload(sc) as sim:
+        sim.substep(sc["dt"], 10)
+        ref = sim.read_state(0)
+    for f in ("x", "v"):
+        assert_close(f, tuned[f], ref[f], rtol=1e-5, rel_scale=1e-5)
+
+
+def test_rigid_motion_follows_set_velocity():
+    # A sphere moving at constant velocity into resting particles: the particles
+    # it touches end up moving with it (grid-level coupling, Sec. IV-A).
+    sc = W.elastic_cube(n=32, n_side=10, corner=(0.4, 0.3, 0.4), substeps=1)
+    sc["gravity"] = (0.0, 0.0, 0.0)
+    sc["rigids"] = [W.sphere((0.5, 0.25, 0.5), 0.06, vel=(0.0, 0.5, 0.0), mu_k=0.0, margin=0.0)]
+    with mpm.from_workload(sc) as sim:
+        sim.substep(1e-4, 400)
+        st = sim.read_state(0)
+        imp = sim.impulse(0)
+    assert st["v"][:, 1].max() > 0.2
+    assert imp[0, 1] < 0  # the soft body pushes back on the rigid

@@ -1,0 +1,157 @@
+"""GPU (CUDA, through the C ABI) vs FP64 oracle parity of the MLS-MPM substep.
+
+Element-by-element comparison of every particle field after one substep from
+identical FP32 inputs, at sizes the oracle finishes in seconds that still span
+many bricks and ragged (partially filled) bricks, plus the whole-run criterion
+on the elastic-cube workload and sampled checks at the full 1M-particle size.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2502_18437_gb300 import mpm, workloads as W
+from tests.parity_util import assert_close, oracle_cfg, oracle_rigids, oracle_state, perturbed
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_one_step(sc, v, C, F, steps_before=0, **opts):
+    """Write (v, C, F), run steps_before substeps, read the state, run one more
+    substep; returns the state before that substep and the GPU result."""
+    with mpm.from_workload(sc) as sim:
+        for k, val in opts.items():
+            sim.set_option(k, val)
+        sim.write_state(0, v=v, C=C, F=F)
+        if steps_before:
+            sim.substep(sc["dt"], steps_before)
+        st = sim.read_state(0)
+        sim.impulse(0)  # reset the accumulated impulse
+        sim.substep(sc["dt"], 1)
+        out = sim.read_state(0)
+        out["grid"] = sim.read_grid(0)
+        out["impulse"] = sim.impulse(0)
+    return st["x"], st["v"], st["C"], st["F"], out
+
+
+def oracle_one_step(sc, x, v, C, F, steps_before=0):
+    cfg = oracle_cfg(sc)
+    st = oracle_state(sc, x, v, C, F)
+    rig, nr = oracle_rigids(sc, steps_before)
+    gm, gv, err = oracle.substep(cfg, st, sc["dt"], rig, nr)
+    imp = np.array([oracle.rigid_impulse(rig[i]) for i in range(nr)]) if nr else np.zeros((0, 6))
+    return st, gm, gv, err, imp
+
+
+def check_fields(out, st):
+    assert_close("x", out["x"], st.x)
+    assert_close("v", out["v"], st.v)
+    assert_close("C", out["C"], st.C)
+    assert_close("F", out["F"], st.F)
+
+
+def check_grid(sc, out, gm, gv):
+    n = sc["n"]
+    g = out["grid"].reshape(-1, 4).astype(np.float64)
+    # grid mass and momentum sums within 1e-6 relative; per node within FP32 tolerance
+    assert abs(g[:, 3].sum() - gm.sum()) <= 1e-6 * gm.sum()
+    mom_g = (g[:, :3] * g[:, 3:4]).sum(0)
+    mom_o = (gv * gm[:, None]).sum(0)
+    assert np.max(np.abs(mom_g - mom_o)) <= 1e-6 * np.abs(gv * gm[:, None]).sum(0).max() + 1e-12
+    assert_close("grid m", g[:, 3], gm)
+    assert_close("grid v", g[:, :3], gv)
+    assert g.shape[0] == n ** 3
+
+
+@pytest.mark.parametrize("model", ["fixed_corotated", "neo_hookean"])
+def test_cube_one_substep_all_fields(model):
+    sc = W.elastic_cube(model=model)
+    v, C, F = perturbed(sc, seed=11)
+    x, v, C, F, out = gpu_one_step(sc, v, C, F)
+    st, gm, gv, err, _ = oracle_one_step(sc, x, v, C, F)
+    assert err == 0
+    check_fields(out, st)
+    check_grid(sc, out, gm, gv)
+
+
+def test_cube_100_substeps_position_error():
+    # Whole-run criterion: max particle position error <= 1e-3 dx after 100 substeps.
+    sc = W.elastic_cube()
+    with mpm.from_workload(sc) as sim:
+        sim.substep(sc["dt"], sc["substeps"])
+        got = sim.read_state(0, ("x", "v"))
+    st = oracle_state(sc)
+    assert oracle.run(oracle_cfg(sc), st, sc["dt"], sc["substeps"]) == 0
+    dx = 1.0 / sc["n"]
+    err = np.max(np.abs(got["x"] - st.x))
+    assert err <= 1e-3 * dx, err
+    assert np.max(np.abs(st.x - sc["x"])) > 10 * err  # the cube did move
+
+
+@pytest.mark.parametrize("steps_before", [0, 12, 40])
+def test_slab_with_blade_and_thread(steps_before):
+    # Tissue slab (Neo-Hookean, per-particle E) cut by the slicer and pushed by
+    # the capsule-chain thread; one substep from the same state at several
+    # points of the trajectory, including the impulse given to each rigid.
+    sc = W.tissue_slab(cells=(40, 8, 40), lo=(0.25, 0.15, 0.25), size=(0.5, 0.1, 0.5), n=64, substeps=50)
+    sc["rigids"][0]["center"] = (0.5, 0.15 + 0.1 - 0.03 + 0.04, 0.5)  # blade edge already in the tissue
+    N = len(sc["x"])
+    g = np.random.default_rng(5)
+    v0 = (0.05 * g.normal(size=(N, 3))).astype(np.float32)
+    x, v, C, F, out = gpu_one_step(sc, v0, np.zeros((N, 3, 3), np.float32),
+                                   np.tile(np.eye(3, dtype=np.float32), (N, 1, 1)), steps_before=steps_before)
+    st, gm, gv, err, imp = oracle_one_step(sc, x, v, C, F, steps_before)
+    assert err == 0
+    check_fields(out, st)
+    check_grid(sc, out, gm, gv)
+    assert np.abs(imp[:, :3]).max() > 0  # there is contact
+    for r in range(len(sc["rigids"])):
+        assert_close(f"impulse[{r}]", out["impulse"][r], imp[r], rtol=1e-4, rel_scale=1e-4)
+
+
+@pytest.mark.parametrize("steps_before", [0, 30])
+def test_plastic_block(steps_before):
+    sc = W.tissue_block(N=65536, n=64)
+    v, C, F = perturbed(sc, seed=3, f_amp=0.03, c_amp=5.0)
+    x, v, C, F, out = gpu_one_step(sc, v, C, F, steps_before=steps_before)
+    st, gm, gv, err, _ = oracle_one_step(sc, x, v, C, F)
+    assert err == 0
+    check_fields(out, st)
+    check_grid(sc, out, gm, gv)
+
+
+def test_full_size_1m_block_one_substep():
+    # Full-size scale-sweep case (1M particles, 256^3) in the launch shape the
+    # benchmark times (graphs, default options): every particle checked.
+    sc = W.tissue_block(N=1048576, n=256)
+    v, C, F = perturbed(sc, seed=7, f_amp=0.03, c_amp=5.0)
+    x, v, C, F, out = gpu_one_step(sc, v, C, F)
+    st, gm, gv, err, _ = oracle_one_step(sc, x, v, C, F)
+    assert err == 0
+    check_fields(out, st)
+    assert abs(out["grid"][..., 3].sum() - gm.sum()) <= 1e-6 * gm.sum()
+
+
+def test_sort_by_brick_order():
+    # After a substep particles are stored sorted by the brick of their base
+    # cell at the start of that substep: compare the key sequence and counts.
+    sc = W.tissue_block(N=65536, n=64)
+    with mpm.from_workload(sc) as sim:
+        sim.substep(sc["dt"], 1)
+        order = sim.read_state(0, ("order",))["order"]
+    key, perm, count = oracle.sort_by_brick(sc["n"], sc["x"])
+    assert np.array_equal(np.sort(order), np.arange(len(order)))
+    assert np.array_equal(key[order], key[perm])  # identical key sequence (same bricks, same offsets)
+
+
+def test_graph_direct_and_looped_agree():
+    sc = W.tissue_slab(cells=(32, 6, 32), lo=(0.3, 0.2, 0.3), size=(0.4, 0.08, 0.4), n=32, substeps=20)
+    outs = []
+    for opts in ({"use_graphs": 1}, {"use_graphs": 0}, {"launch_mode": 1}):
+        with mpm.from_workload(sc) as sim:
+            for k, v in opts.items():
+                sim.set_option(k, v)
+            sim.substep(sc["dt"], 20)
+            outs.append(sim.read_state(0))
+    for o in outs[1:]:
+        for f in ("x", "v", "F"):
+            assert_close(f, o[f], outs[0][f], rtol=1e-4, rel_scale=1e-4)
