@@ -82,12 +82,14 @@ enum {
     MPM_OPT_USE_GRAPHS = 1,     /* 0/1: replay substeps from captured CUDA graphs   */
     MPM_OPT_LAUNCH_MODE = 2,    /* 0: one launch per phase over all scenes;
                                    1: one launch per phase per scene (looped)       */
-    MPM_OPT_P2G_THREADS = 3,    /* threads per CTA of the P2G kernel: 128/256/512   */
+    MPM_OPT_P2G_THREADS = 3,    /* threads per CTA of the P2G kernel: fixed at 192
+                                   (64 cells x 3 node slices); other values rejected */
     MPM_OPT_G2P_THREADS = 4,    /* threads per CTA of the G2P kernel: 128/256/512   */
     MPM_OPT_CTAS_PER_SM = 5,    /* persistent CTAs per SM for P2G/G2P (0 = occupancy max) */
     MPM_OPT_GRAPH_CHUNK = 6,    /* substeps captured per graph (1..64)              */
-    MPM_OPT_PHASE_TIMING = 7    /* 0/1: record CUDA events around each phase of every
+    MPM_OPT_PHASE_TIMING = 7,   /* 0/1: record CUDA events around each phase of every
                                    substep (forces direct launches); see mpm_phase_stats */
+    MPM_OPT_P2G_CHUNK = 8       /* particles staged per pass of the P2G kernel: 192/384 */
 };
 
 /* ---- configuration --------------------------------------------------- */
@@ -144,8 +146,9 @@ typedef struct mpm_ctx mpm_ctx; /* opaque; owned by the library */
 /* ---- lifecycle ------------------------------------------------------- */
 
 /* Create a context on the current CUDA device; `cuda_stream` is a cudaStream_t
- * (NULL = the legacy default stream) on which all of the context's work is
- * ordered.  Allocates every device buffer the substep needs for
+ * on which all of the context's work is ordered (NULL: the context creates and
+ * owns a non-blocking stream, since substeps are replayed from CUDA graphs,
+ * which cannot be captured on the legacy default stream).  Allocates every device buffer the substep needs for
  * cfg->max_particles particles and the scenes' grids up front.
  * Errors: INVALID_ARGUMENT (cfg values), OUT_OF_MEMORY, CUDA. */
 int mpm_create(const mpm_config* cfg, void* cuda_stream, mpm_ctx** out);
@@ -252,7 +255,7 @@ int mpm_backward(mpm_ctx* ctx, const float* dL_dx, const float* dL_dv, float* dL
 
 /* ---- batching -------------------------------------------------------- */
 
-/* Time candidate launch shapes (threads per CTA of P2G and G2P, persistent
+/* Time candidate launch shapes (P2G chunk, threads per CTA of G2P, persistent
  * CTAs per SM) on `trial_substeps` substeps of size dt and keep the fastest;
  * the particle state, keys, clocks and impulses are restored afterwards, so
  * the simulation does not advance.  *best_ms_out (may be NULL) receives the

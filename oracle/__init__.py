@@ -69,6 +69,8 @@ def lib():
         L.orc_kirchhoff.restype = ct.c_int
         L.orc_kirchhoff.argtypes = [ct.c_int, D, ct.c_double, ct.c_double, D]
         L.orc_lame.argtypes = [ct.c_double, ct.c_double, D, D]
+        L.orc_kirchhoff_all.restype = ct.c_int
+        L.orc_kirchhoff_all.argtypes = [ct.c_int, ct.c_int, D, D, D, D]
         L.orc_von_mises.restype = ct.c_int
         L.orc_von_mises.argtypes = [D, ct.c_double, ct.c_double]
         L.orc_rigid_set_quat.argtypes = [ct.POINTER(Rigid), D]
@@ -192,6 +194,18 @@ def kirchhoff(model, F, mu, lam):
     tau = np.zeros((3, 3))
     m = MODELS[model] if isinstance(model, str) else int(model)
     err = lib().orc_kirchhoff(m, _dp(F), float(mu), float(lam), _dp(tau))
+    return tau, err
+
+
+def kirchhoff_all(model, F, mu, lam):
+    """Kirchhoff stress of every particle: F (N,3,3) -> tau (N,3,3), error bits."""
+    F = _arr(F).reshape(-1, 3, 3)
+    N = len(F)
+    mu = np.broadcast_to(_arr(mu), (N,)).copy()
+    lam = np.broadcast_to(_arr(lam), (N,)).copy()
+    tau = np.zeros((N, 3, 3))
+    m = MODELS[model] if isinstance(model, str) else int(model)
+    err = lib().orc_kirchhoff_all(m, N, _dp(np.ascontiguousarray(F)), _dp(mu), _dp(lam), _dp(tau))
     return tau, err
 
 

@@ -244,6 +244,14 @@ int orc_kirchhoff(int model, const double F[9], double mu, double lam, double ta
     return 0;
 }
 
+/* Kirchhoff stress of N particles (tau: N x 9); returns the OR of error bits. */
+int orc_kirchhoff_all(int model, int N, const double* F, const double* mu, const double* lam, double* tau)
+{
+    int err = 0;
+    for (int p = 0; p < N; ++p) err |= orc_kirchhoff(model, F + 9 * p, mu[p], lam[p], tau + 9 * p);
+    return err;
+}
+
 /* Lame parameters from Young's modulus and Poisson ratio (textbook). */
 void orc_lame(double E, double nu, double* mu, double* lam)
 {

@@ -47,7 +47,7 @@ int wait_stream(mpm_ctx* c)
     }
 }
 
-size_t state_bytes(int cap) { return (size_t)cap * (26 * sizeof(float) + sizeof(int)); }
+size_t state_bytes(int cap) { return (size_t)cap * (kStateFloats * sizeof(float) + sizeof(int)); }
 
 PState state_view(float* base, int cap)
 {
@@ -56,9 +56,10 @@ PState state_view(float* base, int cap)
     s.v = base + 3 * (size_t)cap;
     s.C = base + 6 * (size_t)cap;
     s.F = base + 15 * (size_t)cap;
-    s.mu = base + 24 * (size_t)cap;
-    s.lam = base + 25 * (size_t)cap;
-    s.id = reinterpret_cast<int*>(base + 26 * (size_t)cap);
+    s.tau = base + 24 * (size_t)cap;
+    s.mu = base + 30 * (size_t)cap;
+    s.lam = base + 31 * (size_t)cap;
+    s.id = reinterpret_cast<int*>(base + 32 * (size_t)cap);
     return s;
 }
 
@@ -115,12 +116,11 @@ void clear_graphs(mpm_ctx* c)
     c->graphs.clear();
 }
 
-static int persistent_ctas(mpm_ctx* c)
+static int cap_occ(const mpm_ctx* c, int occ)
 {
-    int occ = std::min(occupancy_p2g(c->p2g_threads), occupancy_g2p(c->g2p_threads));
     if (occ < 1) occ = 1;
     if (c->ctas_per_sm > 0 && c->ctas_per_sm < occ) occ = c->ctas_per_sm;
-    return c->num_sms * occ;
+    return occ;
 }
 
 StepArgs step_args(mpm_ctx* c, float dt, int s0, int s1, const PState& in, const PState& out)
@@ -153,8 +153,10 @@ StepArgs step_args(mpm_ctx* c, float dt, int s0, int s1, const PState& in, const
     a.model = c->cfg.model;
     a.plasticity = c->cfg.plasticity;
     a.yield_stress = c->cfg.yield_stress;
-    a.persistent_ctas = persistent_ctas(c);
-    a.p2g_threads = c->p2g_threads;
+    a.persistent_ctas = c->num_sms * cap_occ(c, occupancy_g2p(c->g2p_threads));
+    a.p2g_ctas = c->num_sms * cap_occ(c, occupancy_p2g(c->p2g_chunk));
+    a.grid_ctas = c->num_sms * 8;
+    a.p2g_chunk = c->p2g_chunk;
     a.g2p_threads = c->g2p_threads;
     return a;
 }
@@ -197,7 +199,7 @@ int ensure_keys(mpm_ctx* c)
     if (c->keys_valid) return MPM_OK;
     MPM_CK(cudaMemsetAsync(c->sb.cnt, 0, sizeof(int) * (size_t)c->total_bricks, c->stream));
     StepArgs a = step_args(c, 0.f, 0, c->n_scenes, c->st[c->cur], c->st[c->cur ^ 1]);
-    MPM_CK(launch_init_keys(a, c->st[c->cur], c->stream));
+    MPM_CK(launch_prepare(a, c->st[c->cur], c->stream));
     c->keys_valid = true;
     return MPM_OK;
 }
@@ -238,6 +240,7 @@ static void free_ctx(mpm_ctx* c)
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     if (c->ev) cudaEventDestroy(c->ev);
     for (cudaEvent_t e : c->phase_events) cudaEventDestroy(e);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }
 
@@ -283,6 +286,11 @@ extern "C" int mpm_create(const mpm_config* cfg, void* stream, mpm_ctx** out)
     for (auto& r : c->h_rigids) r.type = MPM_RIGID_NONE;
 
     cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess && !c->stream) {
+        // graphs cannot be captured on the legacy default stream: use a private one
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        c->own_stream = e == cudaSuccess;
+    }
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     const size_t nbk = (size_t)c->total_bricks;
     c->n_tiles_max = (int)((nbk + kScanTile - 1) / kScanTile);
@@ -355,9 +363,15 @@ extern "C" int mpm_set_option(mpm_ctx* c, int option, int64_t value)
         c->launch_mode = (int)value;
         break;
     case MPM_OPT_P2G_THREADS:
+        if (value != kP2GThreads) return MPM_ERR_INVALID_ARGUMENT;
+        break;
+    case MPM_OPT_P2G_CHUNK:
+        if (value != kP2GThreads && value != 2 * kP2GThreads) return MPM_ERR_INVALID_ARGUMENT;
+        c->p2g_chunk = (int)value;
+        break;
     case MPM_OPT_G2P_THREADS:
         if (value != 128 && value != 256 && value != 512) return MPM_ERR_INVALID_ARGUMENT;
-        (option == MPM_OPT_P2G_THREADS ? c->p2g_threads : c->g2p_threads) = (int)value;
+        c->g2p_threads = (int)value;
         break;
     case MPM_OPT_CTAS_PER_SM:
         if (value < 0 || value > 32) return MPM_ERR_INVALID_ARGUMENT;
@@ -429,15 +443,15 @@ extern "C" int mpm_add_particles(mpm_ctx* c, int scene, int64_t n, const float* 
     if (tail > 0) {
         // make room: copy into the spare buffer with the later scenes shifted by n
         PState nxt = c->st[c->cur ^ 1];
-        float* arr_src[27] = {};
-        float* arr_dst[27] = {};
-        for (int k = 0; k < 26; ++k) {
+        float* arr_src[kStateFloats + 1] = {};
+        float* arr_dst[kStateFloats + 1] = {};
+        for (int k = 0; k < kStateFloats; ++k) {
             arr_src[k] = cur.x + (size_t)k * c->cap;
             arr_dst[k] = nxt.x + (size_t)k * c->cap;
         }
-        arr_src[26] = reinterpret_cast<float*>(cur.id);
-        arr_dst[26] = reinterpret_cast<float*>(nxt.id);
-        for (int k = 0; k < 27; ++k) {
+        arr_src[kStateFloats] = reinterpret_cast<float*>(cur.id);
+        arr_dst[kStateFloats] = reinterpret_cast<float*>(nxt.id);
+        for (int k = 0; k <= kStateFloats; ++k) {
             if (p_at > 0)
                 MPM_CK(cudaMemcpyAsync(arr_dst[k], arr_src[k], sizeof(float) * p_at, cudaMemcpyDeviceToDevice, c->stream));
             MPM_CK(cudaMemcpyAsync(arr_dst[k] + p_at + n, arr_src[k] + p_at, sizeof(float) * tail,
@@ -586,8 +600,9 @@ extern "C" int mpm_substep(mpm_ctx* c, float dt, int n_substeps)
 
 static int error_status(unsigned bits)
 {
-    if (bits & MPM_EBIT_OUT_OF_DOMAIN) return MPM_ERR_OUT_OF_DOMAIN;
+    // a non-finite value is reported first: its NaN position also fails the domain test
     if (bits & MPM_EBIT_NONFINITE) return MPM_ERR_NONFINITE;
+    if (bits & MPM_EBIT_OUT_OF_DOMAIN) return MPM_ERR_OUT_OF_DOMAIN;
     if (bits & MPM_EBIT_INVERTED) return MPM_ERR_INVERTED;
     if (bits & MPM_EBIT_TIMEOUT) return MPM_ERR_TIMEOUT;
     return MPM_OK;
@@ -694,7 +709,8 @@ extern "C" int mpm_write_state(mpm_ctx* c, int scene, uint32_t fields, const voi
         off += align256(bytes);
         MPM_CK(launch_scatter_field(cur, c->cap, sc.p_begin, np, f, static_cast<const float*>(d), c->stream));
     }
-    if (fields & MPM_FIELD_X) c->keys_valid = false;
+    // new positions need new brick keys; a new F needs its stress
+    if (fields & (MPM_FIELD_X | MPM_FIELD_F)) c->keys_valid = false;
     if (mem == MPM_MEM_HOST) return wait_stream(c);
     return MPM_OK;
 }
@@ -757,15 +773,15 @@ extern "C" int mpm_autotune(mpm_ctx* c, float dt, int trial_substeps, float* bes
     cudaError_t ce = copy_all(true);
     if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
     if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
-    const int saved[3] = {c->p2g_threads, c->g2p_threads, c->ctas_per_sm};
-    int best[3] = {saved[0], saved[1], saved[2]};
+    int best[3] = {c->p2g_chunk, c->g2p_threads, c->ctas_per_sm};
     float best_ms = 3.4e38f;
+    const int chunks[2] = {kP2GThreads, 2 * kP2GThreads};
     const int threads[3] = {128, 256, 512};
-    const int ctas[3] = {0, 2, 4};
-    for (int a = 0; a < 3 && ce == cudaSuccess && st == MPM_OK; ++a)
+    const int ctas[2] = {0, 2};
+    for (int a = 0; a < 2 && ce == cudaSuccess && st == MPM_OK; ++a)
         for (int b = 0; b < 3 && ce == cudaSuccess && st == MPM_OK; ++b)
-            for (int k = 0; k < 3 && ce == cudaSuccess && st == MPM_OK; ++k) {
-                c->p2g_threads = threads[a];
+            for (int k = 0; k < 2 && ce == cudaSuccess && st == MPM_OK; ++k) {
+                c->p2g_chunk = chunks[a];
                 c->g2p_threads = threads[b];
                 c->ctas_per_sm = ctas[k];
                 // one untimed warm-up substep, then the timed trial
@@ -783,7 +799,7 @@ extern "C" int mpm_autotune(mpm_ctx* c, float dt, int trial_substeps, float* bes
                 ms /= trial_substeps;
                 if (!st && ce == cudaSuccess && ms < best_ms) {
                     best_ms = ms;
-                    best[0] = threads[a];
+                    best[0] = chunks[a];
                     best[1] = threads[b];
                     best[2] = ctas[k];
                 }
@@ -792,7 +808,7 @@ extern "C" int mpm_autotune(mpm_ctx* c, float dt, int trial_substeps, float* bes
             }
     if (ce == cudaSuccess && st == MPM_OK) st = wait_stream(c);
     c->cur = cur0;
-    c->p2g_threads = best[0];
+    c->p2g_chunk = best[0];
     c->g2p_threads = best[1];
     c->ctas_per_sm = best[2];
     clear_graphs(c);

@@ -12,6 +12,7 @@ struct mpm_tape;  // recorded trajectory for mpm_backward (mpm_adjoint.cu)
 struct mpm_ctx {
     mpm_config cfg{};
     cudaStream_t stream = nullptr;
+    bool own_stream = false;
     int device = 0, num_sms = 0;
     int n_scenes = 0;
     std::vector<int> scene_n, brick_base;  // brick_base has n_scenes + 1 entries
@@ -50,7 +51,7 @@ struct mpm_ctx {
     // options
     int use_graphs = 1;
     int launch_mode = 0;
-    int p2g_threads = 256;
+    int p2g_chunk = 2 * mpm::kP2GThreads;
     int g2p_threads = 256;
     int ctas_per_sm = 0;
     int graph_chunk = 16;

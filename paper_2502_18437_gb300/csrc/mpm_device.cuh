@@ -3,7 +3,7 @@
 //
 // Layout in HBM
 //  - particles: structure of arrays, component-major: x[3][cap], v[3][cap],
-//    C[9][cap], F[9][cap], mu[cap], lam[cap], id[cap].  Two copies ping-pong:
+//    C[9][cap], F[9][cap], tau[6][cap], mu[cap], lam[cap], id[cap].  Two copies ping-pong:
 //    each substep reads one through the sort permutation and G2P writes the
 //    other in sorted order, so particles stay sorted by brick in storage.
 //  - grid: each scene owns a dense block of (n/4)^3 bricks of 4^3 nodes;
@@ -64,6 +64,7 @@ struct PState {
     float* v;
     float* C;
     float* F;
+    float* tau;  // Kirchhoff stress of F, symmetric (xx xy xz yy yz zz)
     float* mu;
     float* lam;
     int* id;
@@ -116,30 +117,42 @@ __device__ __forceinline__ float det3(const float F[9])
 // Rotation-variant SVD F = U diag(s) V^T (det U = det V = +1, s sorted by
 // decreasing magnitude, s[2] < 0 when det F < 0) in FP32, after McAdams et al.
 // 2011 ("Computing the SVD of 3x3 matrices with minimal branching"): cyclic
-// Jacobi eigen-analysis of the symmetric F^T F for V (here with exact Givens
-// angles, 4 sweeps), sorting of the columns of B = F V, and a Givens QR of B
+// Jacobi eigen-analysis of the symmetric F^T F for V (here with the textbook
+// Givens tangent rather than approximate quaternion rotations, 4 sweeps), sorting of the columns of B = F V, and a Givens QR of B
 // for U and s, which recovers small singular values accurately from B rather
 // than from the squared eigenvalues.
 
+__device__ __forceinline__ float approx_sqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+
+// One Jacobi rotation of the symmetric (p,q) block, annihilating a_pq.  With
+// d = a_qq - a_pp and b = 2 a_pq the textbook tangent of the smaller angle,
+// t = sign(theta) / (|theta| + sqrt(theta^2 + 1)) with theta = d/b, equals
+// sign(d) b / (|d| + sqrt(d^2 + b^2)); the rotation is (c, s) = (1, t)/sqrt(1+t^2),
+// exactly orthogonal up to rounding whatever the accuracy of t.
 __device__ __forceinline__ void jacobi_rot(float& app, float& aqq, float& apq, float& arp, float& arq,
                                            float& v0p, float& v0q, float& v1p, float& v1q, float& v2p,
                                            float& v2q)
 {
-    if (apq == 0.0f) return;
-    float theta = (aqq - app) / (2.0f * apq);
-    float t = copysignf(1.0f, theta) / (fabsf(theta) + sqrtf(__fmaf_rn(theta, theta, 1.0f)));
-    float c = rsqrtf(__fmaf_rn(t, t, 1.0f));
-    float s = t * c;
+    // already converged to single precision (also keeps b^2 clear of underflow)
+    if (!(fabsf(apq) > 1e-10f * fmaxf(fabsf(app), fabsf(aqq)))) return;
+    const float d = aqq - app, b = 2.0f * apq;
+    // scale by max(|d|, |b|) > 0 so that d^2 + b^2 neither underflows nor overflows
+    const float inv = __fdividef(1.0f, fmaxf(fabsf(d), fabsf(b)));
+    const float ds = d * inv, bs = b * inv;
+    const float den = fabsf(ds) + approx_sqrt(__fmaf_rn(ds, ds, bs * bs));
+    const float t = __fdividef(d >= 0.0f ? bs : -bs, den);
+    const float c = rsqrtf(__fmaf_rn(t, t, 1.0f));
+    const float s = t * c;
     app = __fmaf_rn(-t, apq, app);
     aqq = __fmaf_rn(t, apq, aqq);
     apq = 0.0f;
     float rp = c * arp - s * arq, rq = s * arp + c * arq;
     arp = rp;
     arq = rq;
-    float a, b;
-    a = v0p; b = v0q; v0p = c * a - s * b; v0q = s * a + c * b;
-    a = v1p; b = v1q; v1p = c * a - s * b; v1q = s * a + c * b;
-    a = v2p; b = v2q; v2p = c * a - s * b; v2q = s * a + c * b;
+    float x, y;
+    x = v0p; y = v0q; v0p = c * x - s * y; v0q = s * x + c * y;
+    x = v1p; y = v1q; v1p = c * x - s * y; v1q = s * x + c * y;
+    x = v2p; y = v2q; v2p = c * x - s * y; v2q = s * x + c * y;
 }
 
 __device__ __forceinline__ void swap_neg_cols(float M[9], int i, int j)
@@ -223,69 +236,78 @@ __device__ __forceinline__ void mul_abt(const float A[9], const float B[9], floa
 
 // ------------------------------------------------------------ stresses
 //
-// Kirchhoff stress tau = J sigma (the paper's Eq. 6 is the Cauchy form; the
-// Kirchhoff form avoids tracking the current volume, V sigma = V0 tau).
-// Returns error bits (MPM_EBIT_INVERTED when the law needs ln J of J <= 0).
-__device__ __forceinline__ unsigned kirchhoff(int model, const float F[9], float mu, float lam, float tau[9])
+// Constitutive update of one particle, the last step of the G2P loop of
+// Algorithm 1: optional plastic projection of F, then the Kirchhoff stress
+// tau = J sigma of the (projected) F, stored symmetric as (xx xy xz yy yz zz).
+// The paper's Eq. 6 is the Cauchy form; with V = J V0 the P2G force term
+// V sigma equals V0 tau.
+//  - fixed-corotated: tau = 2 mu (F - R) F^T + lambda (J - 1) J I with R the
+//    rotation of the polar decomposition.  With F = U S V^T (rotation-variant
+//    SVD) and R = U V^T this is U diag(2 mu (s - 1) s) U^T + lambda (J-1) J I.
+//  - Neo-Hookean: tau = mu (F F^T - I) + lambda ln(J) I (J <= 0: flagged).
+//  - von Mises on the Hencky strain (plasticity is the paper's future work;
+//    the law is the library's definition): eps = ln s, dev = eps - tr(eps)/3,
+//    gamma = |dev| - yield / (2 mu); when gamma > 0, eps -= gamma dev/|dev| and
+//    F = U diag(exp eps) V^T.
+// Returns error bits.
+__device__ __forceinline__ unsigned constitutive(int model, int plastic, float yield, float mu, float lam,
+                                                 float F[9], float t6[6])
 {
-    float J = det3(F);
-    if (model == MPM_NEO_HOOKEAN) {
-        // tau = mu (F F^T - I) + lambda ln(J) I
-        unsigned e = 0;
-        float lnJ = 0.0f;
-        if (J > 0.0f) lnJ = logf(J);
-        else e = MPM_EBIT_INVERTED;
-        mul_abt(F, F, tau);
+    unsigned e = 0u;
+    if (model == MPM_FIXED_COROTATED || plastic) {
+        float U[9], s[3], V[9];
+        svd3(F, U, s, V);
+        if (plastic) {
+            if (!(s[2] > 0.0f)) {
+                e |= MPM_EBIT_INVERTED;
+            } else {
+                const float e0 = __logf(s[0]), e1 = __logf(s[1]), e2 = __logf(s[2]);
+                const float tr = (e0 + e1 + e2) * (1.0f / 3.0f);
+                const float d0 = e0 - tr, d1 = e1 - tr, d2 = e2 - tr;
+                const float nrm = approx_sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+                const float gamma = nrm - __fdividef(yield, 2.0f * mu);
+                if (gamma > 0.0f && nrm > 0.0f) {
+                    const float k = __fdividef(gamma, nrm);
+                    s[0] = __expf(e0 - k * d0);
+                    s[1] = __expf(e1 - k * d1);
+                    s[2] = __expf(e2 - k * d2);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) tau[i] *= mu;
-        float d = __fmaf_rn(lam, lnJ, -mu);
-        tau[0] += d;
-        tau[4] += d;
-        tau[8] += d;
-        return e;
+                    for (int r = 0; r < 3; ++r)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c)
+                            F[3 * r + c] = U[3 * r] * s[0] * V[3 * c] + U[3 * r + 1] * s[1] * V[3 * c + 1] +
+                                           U[3 * r + 2] * s[2] * V[3 * c + 2];
+                }
+            }
+        }
+        if (model == MPM_FIXED_COROTATED) {
+            const float J = s[0] * s[1] * s[2];
+            const float l = lam * (J - 1.0f) * J;
+            const float g0 = 2.0f * mu * (s[0] - 1.0f) * s[0];
+            const float g1 = 2.0f * mu * (s[1] - 1.0f) * s[1];
+            const float g2 = 2.0f * mu * (s[2] - 1.0f) * s[2];
+            // U diag(g) U^T + l I
+            t6[0] = g0 * U[0] * U[0] + g1 * U[1] * U[1] + g2 * U[2] * U[2] + l;
+            t6[1] = g0 * U[0] * U[3] + g1 * U[1] * U[4] + g2 * U[2] * U[5];
+            t6[2] = g0 * U[0] * U[6] + g1 * U[1] * U[7] + g2 * U[2] * U[8];
+            t6[3] = g0 * U[3] * U[3] + g1 * U[4] * U[4] + g2 * U[5] * U[5] + l;
+            t6[4] = g0 * U[3] * U[6] + g1 * U[4] * U[7] + g2 * U[5] * U[8];
+            t6[5] = g0 * U[6] * U[6] + g1 * U[7] * U[7] + g2 * U[8] * U[8] + l;
+            return e;
+        }
     }
-    // fixed-corotated: tau = 2 mu (F - R) F^T + lambda (J - 1) J I
-    float U[9], s[3], V[9], R[9], D[9];
-    svd3(F, U, s, V);
-    mul_abt(U, V, R);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) D[i] = F[i] - R[i];
-    mul_abt(D, F, tau);
-    float mu2 = 2.0f * mu;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) tau[i] *= mu2;
-    float d = lam * (J - 1.0f) * J;
-    tau[0] += d;
-    tau[4] += d;
-    tau[8] += d;
-    return 0u;
-}
-
-// Von Mises return mapping on the Hencky strain (elastoplasticity is the
-// paper's future work, Sec. VI; the law is the library's definition): project
-// the deviatoric log-stretch back to 2 mu |dev ln s| = yield.
-__device__ __forceinline__ unsigned von_mises(float F[9], float mu, float yield)
-{
-    float U[9], s[3], V[9];
-    svd3(F, U, s, V);
-    if (!(s[2] > 0.0f)) return MPM_EBIT_INVERTED;
-    float e0 = logf(s[0]), e1 = logf(s[1]), e2 = logf(s[2]);
-    float tr = (e0 + e1 + e2) * (1.0f / 3.0f);
-    float d0 = e0 - tr, d1 = e1 - tr, d2 = e2 - tr;
-    float nrm = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-    float gamma = nrm - yield / (2.0f * mu);
-    if (!(gamma > 0.0f) || nrm == 0.0f) return 0u;
-    float k = gamma / nrm;
-    float x0 = expf(e0 - k * d0), x1 = expf(e1 - k * d1), x2 = expf(e2 - k * d2);
-    float US[9];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        US[3 * r] = U[3 * r] * x0;
-        US[3 * r + 1] = U[3 * r + 1] * x1;
-        US[3 * r + 2] = U[3 * r + 2] * x2;
-    }
-    mul_abt(US, V, F);
-    return 0u;
+    const float J = det3(F);
+    float lnJ = 0.0f;
+    if (J > 0.0f) lnJ = __logf(J);
+    else e |= MPM_EBIT_INVERTED;
+    const float d = __fmaf_rn(lam, lnJ, -mu);
+    t6[0] = mu * (F[0] * F[0] + F[1] * F[1] + F[2] * F[2]) + d;
+    t6[1] = mu * (F[0] * F[3] + F[1] * F[4] + F[2] * F[5]);
+    t6[2] = mu * (F[0] * F[6] + F[1] * F[7] + F[2] * F[8]);
+    t6[3] = mu * (F[3] * F[3] + F[4] * F[4] + F[5] * F[5]) + d;
+    t6[4] = mu * (F[3] * F[6] + F[4] * F[7] + F[5] * F[8]);
+    t6[5] = mu * (F[6] * F[6] + F[7] * F[7] + F[8] * F[8]) + d;
+    return e;
 }
 
 // Rotation matrix of the unit quaternion (w, x, y, z).

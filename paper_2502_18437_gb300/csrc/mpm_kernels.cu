@@ -185,46 +185,65 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(StepArgs a)
     __syncthreads();
     int4 excl = make_int4(incl.x - local.x, incl.y - local.y, incl.z - local.z, 0);
     if (warp > 0) excl = add4(excl, s_warp[warp - 1]);
-    // decoupled look-back across tiles
-    if (tid == 0) {
+    // decoupled look-back across tiles, 32 predecessors per step (warp 0)
+    if (warp == 0) {
         const int4 agg = s_warp[kScanThreads / 32 - 1];
         int4 prefix = make_int4(0, 0, 0, 0);
         if (tile == 0) {
-            sb.tile_incl[0] = agg;
-            __threadfence();
-            st_release(&sb.tile_status[0], 2u);
+            if (lane == 0) {
+                sb.tile_incl[0] = agg;
+                __threadfence();
+                st_release(&sb.tile_status[0], 2u);
+            }
         } else {
-            sb.tile_agg[tile] = agg;
-            __threadfence();
-            st_release(&sb.tile_status[tile], 1u);
-            int j = tile - 1;
+            if (lane == 0) {
+                sb.tile_agg[tile] = agg;
+                __threadfence();
+                st_release(&sb.tile_status[tile], 1u);
+            }
+            int top = tile - 1;
             int spins = 0;
-            while (j >= 0) {
-                unsigned st = ld_acquire(&sb.tile_status[j]);
-                if (st == 2u) {
-                    prefix = add4(prefix, __ldcg(&sb.tile_incl[j]));
-                    break;
-                }
-                if (st == 1u) {
-                    prefix = add4(prefix, __ldcg(&sb.tile_agg[j]));
-                    --j;
+            for (;;) {
+                const int idx = top - lane;
+                const unsigned st = idx >= 0 ? ld_acquire(&sb.tile_status[idx]) : 2u;  // before tile 0: zero
+                const unsigned m2 = __ballot_sync(kFull, st == 2u);
+                const unsigned m0 = __ballot_sync(kFull, st == 0u);
+                const int first2 = m2 ? __ffs(m2) - 1 : 32;
+                const unsigned need = first2 >= 31 ? kFull : ((2u << first2) - 1u);  // lanes 0..first2
+                if (m0 & need) {
+                    if (++spins > (1 << 22)) {  // a predecessor never published: flag and give up
+                        if (lane == 0) atomicOr(&a.err[a.r.s0], MPM_EBIT_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(20);
                     continue;
                 }
-                if (++spins > (1 << 24)) {  // predecessor never published: give up, flag
-                    atomicOr(&a.err[a.r.s0], MPM_EBIT_TIMEOUT);
-                    break;
+                int4 v = make_int4(0, 0, 0, 0);
+                if (lane < first2 && idx >= 0) v = __ldcg(&sb.tile_agg[idx]);
+                if (lane == first2 && idx >= 0) v = __ldcg(&sb.tile_incl[idx]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    v.x += __shfl_xor_sync(kFull, v.x, o);
+                    v.y += __shfl_xor_sync(kFull, v.y, o);
+                    v.z += __shfl_xor_sync(kFull, v.z, o);
                 }
-                __nanosleep(32);
+                prefix = add4(prefix, v);
+                if (m2) break;
+                top -= 32;
             }
-            sb.tile_incl[tile] = add4(prefix, agg);
-            __threadfence();
-            st_release(&sb.tile_status[tile], 2u);
+            if (lane == 0) {
+                sb.tile_incl[tile] = add4(prefix, agg);
+                __threadfence();
+                st_release(&sb.tile_status[tile], 2u);
+            }
         }
-        s_prefix = prefix;
-        if (tile == n_tiles - 1) {
-            const int4 tot = add4(prefix, agg);
-            sb.counters[CTR_N_ACT] = tot.y;
-            sb.counters[CTR_N_NACT] = tot.z;
+        if (lane == 0) {
+            s_prefix = prefix;
+            if (tile == n_tiles - 1) {
+                const int4 tot = add4(prefix, agg);
+                sb.counters[CTR_N_ACT] = tot.y;
+                sb.counters[CTR_N_NACT] = tot.z;
+            }
         }
     }
     __syncthreads();
@@ -287,13 +306,15 @@ __device__ __forceinline__ int aggregated_rank(int* cnt, int key, bool valid)
     return rank;
 }
 
-__global__ void k_init_keys(StepArgs a, PState st)
+// Keys, ranks and stresses of the stored particles after the host changed
+// positions or F (new particles, state writes).
+__global__ void k_prepare(StepArgs a, PState st)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = a.r.p0 + g;
     const bool valid = g < a.r.np;
     int key = 0, scene = -1;
-    unsigned ood = 0;
+    unsigned ebits = 0;
     if (valid) {
         int lo = a.r.s0, hi = a.r.s1 - 1;
         while (lo < hi) {
@@ -301,33 +322,61 @@ __global__ void k_init_keys(StepArgs a, PState st)
             if (a.scenes[mid].p_begin <= i) lo = mid;
             else hi = mid - 1;
         }
-        // skip empty scenes sharing the same p_begin
-        while (lo + 1 < a.r.s1 && a.scenes[lo].p_count == 0 && a.scenes[lo + 1].p_begin <= i) ++lo;
         scene = lo;
         const SceneDev sc = a.scenes[scene];
+        unsigned ood = 0;
         key = brick_key(sc, st.x[i], st.x[a.cap + i], st.x[2 * a.cap + i], ood);
+        if (ood) ebits |= MPM_EBIT_OUT_OF_DOMAIN;
+        float F[9], t6[6];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) F[k] = st.F[(size_t)k * a.cap + i];
+        const float mu = sc.pp_mat ? st.mu[i] : sc.mu, lam = sc.pp_mat ? st.lam[i] : sc.lam;
+        ebits |= constitutive(a.model, 0, 0.f, mu, lam, F, t6);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) st.tau[(size_t)k * a.cap + i] = t6[k];
     }
     const int rank = aggregated_rank(a.sb.cnt, key, valid);
     if (valid) {
         a.sb.key[i] = key;
         a.sb.rank[i] = rank;
-        if (ood) atomicOr(&a.err[scene], MPM_EBIT_OUT_OF_DOMAIN);
+        if (ebits) atomicOr(&a.err[scene], ebits);
     }
 }
 
 // ------------------------------------------------------------------ P2G
+//
+// One CTA per active particle brick (4^3 cells, a 6^3-node window).  Per chunk
+// of up to kP2GChunk particles:
+//   A. one thread per particle: weights, A_p = m C_p - dt V0 M^-1 tau_p
+//      (Eq. 8, M^-1 = 4/dx^2 of Eq. 7) folded into a per-particle record in
+//      shared memory; the chunk is counting-sorted by cell (64 bins);
+//   B. thread (cell c, slice i) sums, in registers, the contributions of the
+//      particles of cell c to its 9 nodes c + (i, j, k): no atomics.
+// At the end of the brick every thread adds its 9 node sums into the shared
+// window (the 32 lanes of a warp hold 32 distinct cells of one slice, so a
+// warp never hits the same node twice), and the window is added to HBM with
+// one vector reduction per node.
 
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_p2g(StepArgs a)
+constexpr int kRecFields = 21;  // w0[3] w1[3] w2[3] q[3] Ad[9]
+
+template <int CHUNK>
+__global__ void __launch_bounds__(kP2GThreads, CHUNK == kP2GThreads ? 5 : 4) k_p2g(StepArgs a)
 {
-    __shared__ float sm[4][kWinNodes];
+    constexpr int PER = CHUNK / kP2GThreads;  // particles per thread per chunk
+    __shared__ float rec[kRecFields][CHUNK];
+    __shared__ short order[CHUNK];
+    __shared__ int cell_cnt[64], cell_off[65];
+    __shared__ float win[4][kWinNodes];
     __shared__ int s_item;
     const int tid = threadIdx.x;
+    const int cell = tid & 63, slice = tid >> 6;
+    const int cx = cell >> 4, cy = (cell >> 2) & 3, cz = cell & 3;
     const int n_act = a.sb.counters[CTR_N_ACT];
     const int cap = a.cap;
     for (;;) {
         if (tid == 0) s_item = atomicAdd(&a.sb.counters[CTR_WORK_P2G], 1);
-        for (int t = tid; t < 4 * kWinNodes; t += BLOCK) (&sm[0][0])[t] = 0.0f;
+        for (int t = tid; t < 4 * kWinNodes; t += kP2GThreads) (&win[0][0])[t] = 0.0f;
+        if (tid < 64) cell_cnt[tid] = 0;
         __syncthreads();
         const int item = s_item;
         if (item >= n_act) break;
@@ -339,71 +388,124 @@ __global__ void __launch_bounds__(BLOCK) k_p2g(StepArgs a)
         const int ox = (lb / (nb * nb)) * 4, oy = ((lb / nb) % nb) * 4, oz = (lb % nb) * 4;
         const float fn = (float)n, dxs = 1.0f / fn;
         const float m = sc.m_p;
-        const float kA = a.dt * sc.V0 * 4.0f * fn * fn;  // dt V0 M^-1, M^-1 = 4/dx^2 (Eq. 7)
+        const float kA = a.dt * sc.V0 * 4.0f * fn * fn;
         unsigned ebits = 0;
-        for (int k = tid; k < count; k += BLOCK) {
-            const int p = a.sb.perm[start + k];
-            const float x0 = a.in.x[p], x1 = a.in.x[cap + p], x2 = a.in.x[2 * cap + p];
-            float v[3] = {a.in.v[p], a.in.v[cap + p], a.in.v[2 * cap + p]};
-            float C[9], F[9];
+        float acc_w[9], acc_p[9][3];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) C[i] = a.in.C[i * cap + p];
+        for (int q = 0; q < 9; ++q) { acc_w[q] = 0.f; acc_p[q][0] = acc_p[q][1] = acc_p[q][2] = 0.f; }
+
+        for (int c0 = 0; c0 < count; c0 += CHUNK) {
+            const int cn = min(CHUNK, count - c0);
+            int my_cell[PER], my_rank[PER];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) F[i] = a.in.F[i * cap + p];
-            const float mu = sc.pp_mat ? a.in.mu[p] : sc.mu;
-            const float lam = sc.pp_mat ? a.in.lam[p] : sc.lam;
-            int b0, b1, b2;
-            ebits |= (base_cell(x0, n, b0) | base_cell(x1, n, b1) | base_cell(x2, n, b2)) ? MPM_EBIT_OUT_OF_DOMAIN : 0u;
-            const float f0 = __fmaf_rn(x0, fn, -(float)b0);
-            const float f1 = __fmaf_rn(x1, fn, -(float)b1);
-            const float f2 = __fmaf_rn(x2, fn, -(float)b2);
-            float w0[3], w1[3], w2[3];
-            bspline(f0, w0);
-            bspline(f1, w1);
-            bspline(f2, w2);
-            float tau[9];
-            ebits |= kirchhoff(a.model, F, mu, lam, tau);
-            // A = m C - dt V0 M^-1 tau, scaled by dx so that x_I - x_p = ((i,j,k) - f) dx
-            float Ad[9];
+            for (int u = 0; u < PER; ++u) {
+                const int k = tid + u * kP2GThreads;
+                my_cell[u] = -1;
+                if (k < cn) {
+                    const int p = a.sb.perm[start + c0 + k];
+                    const float x0 = a.in.x[p], x1 = a.in.x[cap + p], x2 = a.in.x[2 * cap + p];
+                    int b0, b1, b2;
+                    ebits |= (base_cell(x0, n, b0) | base_cell(x1, n, b1) | base_cell(x2, n, b2)) ? MPM_EBIT_OUT_OF_DOMAIN : 0u;
+                    const float f0 = __fmaf_rn(x0, fn, -(float)b0);
+                    const float f1 = __fmaf_rn(x1, fn, -(float)b1);
+                    const float f2 = __fmaf_rn(x2, fn, -(float)b2);
+                    float w[3];
+                    bspline(f0, w);
+                    rec[0][k] = w[0]; rec[1][k] = w[1]; rec[2][k] = w[2];
+                    bspline(f1, w);
+                    rec[3][k] = w[0]; rec[4][k] = w[1]; rec[5][k] = w[2];
+                    bspline(f2, w);
+                    rec[6][k] = w[0]; rec[7][k] = w[1]; rec[8][k] = w[2];
+                    float t6[6];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) Ad[i] = (m * C[i] - kA * tau[i]) * dxs;
-            // per node momentum = W (m v + Ad ((i,j,k) - f)) = W (q + i Ad_0 + j Ad_1 + k Ad_2)
-            float q[3];
+                    for (int q = 0; q < 6; ++q) t6[q] = a.in.tau[(size_t)q * cap + p];
+                    const float tau[9] = {t6[0], t6[1], t6[2], t6[1], t6[3], t6[4], t6[2], t6[4], t6[5]};
+                    float Ad[9];
 #pragma unroll
-            for (int r = 0; r < 3; ++r) q[r] = m * v[r] - (Ad[3 * r] * f0 + Ad[3 * r + 1] * f1 + Ad[3 * r + 2] * f2);
-            int l0 = b0 - ox, l1 = b1 - oy, l2 = b2 - oz;
-            l0 = min(max(l0, 0), 3);
-            l1 = min(max(l1, 0), 3);
-            l2 = min(max(l2, 0), 3);
+                    for (int q = 0; q < 9; ++q) Ad[q] = (m * a.in.C[(size_t)q * cap + p] - kA * tau[q]) * dxs;
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
+                    for (int r = 0; r < 3; ++r) {
+                        const float vr = a.in.v[(size_t)r * cap + p];
+                        rec[9 + r][k] = m * vr - (Ad[3 * r] * f0 + Ad[3 * r + 1] * f1 + Ad[3 * r + 2] * f2);
+                    }
 #pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    const float wij = w0[i] * w1[j];
-                    const float ri0 = q[0] + Ad[0] * i + Ad[1] * j;
-                    const float ri1 = q[1] + Ad[3] * i + Ad[4] * j;
-                    const float ri2 = q[2] + Ad[6] * i + Ad[7] * j;
-                    const int row = (l0 + i) * 36 + (l1 + j) * 6 + l2;
+                    for (int q = 0; q < 9; ++q) rec[12 + q][k] = Ad[q];
+                    const int l0 = min(max(b0 - ox, 0), 3), l1 = min(max(b1 - oy, 0), 3), l2 = min(max(b2 - oz, 0), 3);
+                    my_cell[u] = (l0 * 4 + l1) * 4 + l2;
+                    my_rank[u] = atomicAdd(&cell_cnt[my_cell[u]], 1);
+                }
+            }
+            __syncthreads();
+            if (tid < 32) {
+                // exclusive scan of the 64 cell counts (2 per lane)
+                const int c_a = cell_cnt[2 * tid], c_b = cell_cnt[2 * tid + 1];
+                int incl = c_a + c_b;
 #pragma unroll
-                    for (int k2 = 0; k2 < 3; ++k2) {
-                        const float W = wij * w2[k2];
-                        const int node = row + k2;
-                        atomicAdd(&sm[0][node], W * m);
-                        atomicAdd(&sm[1][node], W * (ri0 + Ad[2] * k2));
-                        atomicAdd(&sm[2][node], W * (ri1 + Ad[5] * k2));
-                        atomicAdd(&sm[3][node], W * (ri2 + Ad[8] * k2));
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int t = __shfl_up_sync(kFull, incl, d);
+                    if (tid >= d) incl += t;
+                }
+                const int excl = incl - c_a - c_b;
+                cell_off[2 * tid] = excl;
+                cell_off[2 * tid + 1] = excl + c_a;
+                if (tid == 31) cell_off[64] = incl;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < PER; ++u)
+                if (my_cell[u] >= 0) order[cell_off[my_cell[u]] + my_rank[u]] = (short)(tid + u * kP2GThreads);
+            __syncthreads();
+            // phase B: contributions of cell `cell` to nodes cell + (slice, j, k)
+            const int beg = cell_off[cell], end = cell_off[cell + 1];
+            for (int j = beg; j < end; ++j) {
+                const int k = order[j];
+                const float wi = rec[slice][k];
+                const float wy0 = rec[3][k], wy1 = rec[4][k], wy2 = rec[5][k];
+                const float wz0 = rec[6][k], wz1 = rec[7][k], wz2 = rec[8][k];
+                const float si = (float)slice;
+                // r(j,k) = q + Ad (slice, j, k)
+                const float r0 = rec[9][k] + si * rec[12][k], r1 = rec[10][k] + si * rec[15][k], r2 = rec[11][k] + si * rec[18][k];
+                const float a01 = rec[13][k], a11 = rec[16][k], a21 = rec[19][k];
+                const float a02 = rec[14][k], a12 = rec[17][k], a22 = rec[20][k];
+                const float wy[3] = {wy0, wy1, wy2}, wz[3] = {wz0, wz1, wz2};
+#pragma unroll
+                for (int jj = 0; jj < 3; ++jj) {
+                    const float wij = wi * wy[jj];
+                    const float s0 = r0 + a01 * jj, s1 = r1 + a11 * jj, s2 = r2 + a21 * jj;
+#pragma unroll
+                    for (int kk = 0; kk < 3; ++kk) {
+                        const float W = wij * wz[kk];
+                        const int q = jj * 3 + kk;
+                        acc_w[q] += W;
+                        acc_p[q][0] += W * (s0 + a02 * kk);
+                        acc_p[q][1] += W * (s1 + a12 * kk);
+                        acc_p[q][2] += W * (s2 + a22 * kk);
                     }
                 }
             }
+            __syncthreads();
+            if (tid < 64) cell_cnt[tid] = 0;
+            __syncthreads();
+        }
+        // node sums of this thread -> shared window
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            if (acc_w[q] != 0.f) {
+                const int node = (cx + slice) * 36 + (cy + q / 3) * 6 + (cz + q % 3);
+                atomicAdd(&win[0][node], acc_w[q] * m);
+                atomicAdd(&win[1][node], acc_p[q][0]);
+                atomicAdd(&win[2][node], acc_p[q][1]);
+                atomicAdd(&win[3][node], acc_p[q][2]);
+            }
         }
         __syncthreads();
-        for (int t = tid; t < kWinNodes; t += BLOCK) {
-            const float mm = sm[0][t];
+        for (int t = tid; t < kWinNodes; t += kP2GThreads) {
+            const float mm = win[0][t];
             if (mm == 0.0f) continue;
             const int gi = ox + t / 36, gj = oy + (t / 6) % 6, gk = oz + t % 6;
             if (gi >= n || gj >= n || gk >= n) continue;
             const int brick = sc.brick_base + ((gi >> 2) * nb + (gj >> 2)) * nb + (gk >> 2);
-            red_add_v4(&a.G[brick * 64 + (gi & 3) * 16 + (gj & 3) * 4 + (gk & 3)], mm, sm[1][t], sm[2][t], sm[3][t]);
+            red_add_v4(&a.G[brick * 64 + (gi & 3) * 16 + (gj & 3) * 4 + (gk & 3)], mm, win[1][t], win[2][t], win[3][t]);
         }
         if (ebits) atomicOr(&a.err[scene], ebits);
         __syncthreads();
@@ -566,121 +668,168 @@ __device__ void stage_rigid(const RigidDev& src, double t_now, RigidCur& dst)
     dst.spine_radius = src.spine_radius;
 }
 
-constexpr int kGridThreads = 64;
+constexpr int kGridThreads = 256;  // 4 node bricks per iteration
 
+__device__ void flush_impulse(const StepArgs& a, const float* simp, int scene, int nr, int tid)
+{
+    for (int t = tid; t < nr * 6; t += kGridThreads)
+        if (simp[t] != 0.f) atomicAdd(&a.impulse[scene * kMaxRigids * 6 + t], (double)simp[t]);
+}
+
+// Grid update of the active node bricks: 64 threads per brick, one node each.
+// Rigids of a scene are staged in shared memory (posed at the scene's clock).
 __global__ void __launch_bounds__(kGridThreads) k_grid(StepArgs a)
 {
     __shared__ RigidCur rig[kMaxRigids];
     __shared__ float simp[kMaxRigids * 6];
-    __shared__ int s_item, s_scene, s_nrig;
-    const int tid = threadIdx.x, lane = tid & 31;
+    __shared__ int s_scene[4];
+    __shared__ int s_staged, s_nrig, s_target;
+    const int tid = threadIdx.x, lane = tid & 31, grp = tid >> 6, nid = tid & 63;
     const int n_nact = a.sb.counters[CTR_N_NACT];
-    if (tid == 0) { s_scene = -1; s_nrig = 0; }
-    for (;;) {
-        if (tid == 0) s_item = atomicAdd(&a.sb.counters[CTR_WORK_GRID], 1);
+    if (tid == 0) { s_staged = -1; s_nrig = 0; }
+    for (int base = blockIdx.x * 4; base < n_nact; base += gridDim.x * 4) {
+        const int item = base + grp;
+        const int my_scene = item < n_nact ? a.sb.nact_scene[item] : -1;
+        if (nid == 0) s_scene[grp] = my_scene;
+        bool done = my_scene < 0;
         __syncthreads();
-        const int item = s_item;
-        const int scene = item < n_nact ? a.sb.nact_scene[item] : -1;
-        if (scene != s_scene) {
-            __syncthreads();
-            if (s_scene >= 0) {
-                for (int t = tid; t < s_nrig * 6; t += kGridThreads)
-                    if (simp[t] != 0.f) atomicAdd(&a.impulse[s_scene * kMaxRigids * 6 + t], (double)simp[t]);
+        for (;;) {
+            // next scene to process among the 4 bricks (usually all the same)
+            if (tid == 0) {
+                int t = -1;
+                for (int g = 0; g < 4; ++g)
+                    if (s_scene[g] >= 0 && (t < 0 || s_scene[g] < t)) t = s_scene[g];
+                s_target = t;
             }
             __syncthreads();
-            if (scene >= 0) {
-                const int nr = a.scenes[scene].n_rigid;
-                const double t_now = a.t_scene[scene];
-                if (tid < nr) stage_rigid(a.rigids[scene * kMaxRigids + tid], t_now, rig[tid]);
+            const int target = s_target;
+            if (target < 0) break;
+            if (target != s_staged) {
+                if (s_staged >= 0) flush_impulse(a, simp, s_staged, s_nrig, tid);
+                __syncthreads();
+                const int nr = a.scenes[target].n_rigid;
+                const double t_now = a.t_scene[target];
+                if (tid < nr) stage_rigid(a.rigids[target * kMaxRigids + tid], t_now, rig[tid]);
                 for (int t = tid; t < nr * kMaxPts * 3; t += kGridThreads) {
                     const int r = t / (kMaxPts * 3), k = t % (kMaxPts * 3);
-                    rig[r].pts[k] = a.rigids[scene * kMaxRigids + r].pts[k];
+                    rig[r].pts[k] = a.rigids[target * kMaxRigids + r].pts[k];
                 }
                 for (int t = tid; t < kMaxRigids * 6; t += kGridThreads) simp[t] = 0.f;
-                if (tid == 0) { s_nrig = nr; s_scene = scene; }
+                if (tid == 0) { s_staged = target; s_nrig = nr; }
+                __syncthreads();
             }
-            __syncthreads();
-        }
-        if (item >= n_nact) break;
-        const int B = a.sb.nact_brick[item];
-        const SceneDev sc = a.scenes[scene];
-        const int n = sc.n, nb = sc.nb, lb = B - sc.brick_base;
-        const int gi = (lb / (nb * nb)) * 4 + (tid >> 4);
-        const int gj = ((lb / nb) % nb) * 4 + ((tid >> 2) & 3);
-        const int gk = (lb % nb) * 4 + (tid & 3);
-        const int node = B * 64 + tid;
-        const float4 g = a.G[node];
-        a.G[node] = make_float4(0.f, 0.f, 0.f, 0.f);
-        float3 v = f3(0.f, 0.f, 0.f);
-        const float dxs = 1.0f / (float)n;
-        float dpr[kMaxRigids][3];
-        unsigned touched = 0;
-        const int nr = s_nrig;
-        if (g.x > 0.f) {
-            v = f3(g.y / g.x + a.dt * a.gravity[0], g.z / g.x + a.dt * a.gravity[1], g.w / g.x + a.dt * a.gravity[2]);
-            const float3 xI = f3(gi * dxs, gj * dxs, gk * dxs);
-            for (int r = 0; r < nr; ++r) {
-                float3 dp;
-                if (rigid_contact(rig[r], xI, g.x, v, dp)) {
-                    touched |= 1u << r;
-                    dpr[r][0] = dp.x; dpr[r][1] = dp.y; dpr[r][2] = dp.z;
+            if (!done && my_scene == target) {
+                done = true;
+                const int B = a.sb.nact_brick[item];
+                const SceneDev sc = a.scenes[target];
+                const int n = sc.n, nb = sc.nb, lb = B - sc.brick_base;
+                const int gi = (lb / (nb * nb)) * 4 + (nid >> 4);
+                const int gj = ((lb / nb) % nb) * 4 + ((nid >> 2) & 3);
+                const int gk = (lb % nb) * 4 + (nid & 3);
+                const int node = B * 64 + nid;
+                const float4 g = a.G[node];
+                a.G[node] = make_float4(0.f, 0.f, 0.f, 0.f);
+                float3 v = f3(0.f, 0.f, 0.f);
+                const float dxs = 1.0f / (float)n;
+                const int nr = s_nrig;
+                float dpr[kMaxRigids][3];
+                unsigned touched = 0;
+                if (g.x > 0.f) {
+                    v = f3(g.y / g.x + a.dt * a.gravity[0], g.z / g.x + a.dt * a.gravity[1], g.w / g.x + a.dt * a.gravity[2]);
+                    const float3 xI = f3(gi * dxs, gj * dxs, gk * dxs);
+                    for (int r = 0; r < nr; ++r) {
+                        float3 dp;
+                        if (rigid_contact(rig[r], xI, g.x, v, dp)) {
+                            touched |= 1u << r;
+                            dpr[r][0] = dp.x; dpr[r][1] = dp.y; dpr[r][2] = dp.z;
+                        }
+                    }
+                    const int lo = a.bound, hi = n - 1 - a.bound;
+                    if (gi < lo) v.x = fmaxf(v.x, 0.f);
+                    if (gi > hi) v.x = fminf(v.x, 0.f);
+                    if (gj < lo) {
+                        if (a.floor_sticky) v = f3(0.f, 0.f, 0.f);
+                        else v.y = fmaxf(v.y, 0.f);
+                    }
+                    if (gj > hi) v.y = fminf(v.y, 0.f);
+                    if (gk < lo) v.z = fmaxf(v.z, 0.f);
+                    if (gk > hi) v.z = fminf(v.z, 0.f);
+                }
+                a.V[node] = make_float4(v.x, v.y, v.z, g.x);
+                if (nid == 0) a.brick_epoch[B] = a.epoch[target];
+                // impulse on each rigid: -(node momentum change), linear and angular
+                for (int r = 0; r < nr; ++r) {
+                    const bool on = (touched >> r) & 1u;
+                    if (!__any_sync(kFull, on)) continue;
+                    float val[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                    if (on) {
+                        const float d0 = -dpr[r][0], d1 = -dpr[r][1], d2 = -dpr[r][2];
+                        const float r0 = gi * dxs - rig[r].c[0], r1 = gj * dxs - rig[r].c[1], r2 = gk * dxs - rig[r].c[2];
+                        val[0] = d0; val[1] = d1; val[2] = d2;
+                        val[3] = r1 * d2 - r2 * d1;
+                        val[4] = r2 * d0 - r0 * d2;
+                        val[5] = r0 * d1 - r1 * d0;
+                    }
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) {
+                        float x = val[c];
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+                        if (lane == 0) atomicAdd(&simp[r * 6 + c], x);
+                    }
                 }
             }
-            const int lo = a.bound, hi = n - 1 - a.bound;
-            if (gi < lo) v.x = fmaxf(v.x, 0.f);
-            if (gi > hi) v.x = fminf(v.x, 0.f);
-            if (gj < lo) {
-                if (a.floor_sticky) v = f3(0.f, 0.f, 0.f);
-                else v.y = fmaxf(v.y, 0.f);
-            }
-            if (gj > hi) v.y = fminf(v.y, 0.f);
-            if (gk < lo) v.z = fmaxf(v.z, 0.f);
-            if (gk > hi) v.z = fminf(v.z, 0.f);
+            __syncthreads();
+            if (nid == 0 && my_scene == target) s_scene[grp] = -1;
+            __syncthreads();
         }
-        a.V[node] = make_float4(v.x, v.y, v.z, g.x);
-        if (tid == 0) a.brick_epoch[B] = a.epoch[scene];
-        // impulse on each rigid: -(node momentum change), linear and angular
-        for (int r = 0; r < nr; ++r) {
-            const bool on = (touched >> r) & 1u;
-            if (!__any_sync(kFull, on)) continue;
-            float val[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (on) {
-                const float d0 = -dpr[r][0], d1 = -dpr[r][1], d2 = -dpr[r][2];
-                const float r0 = gi * dxs - rig[r].c[0], r1 = gj * dxs - rig[r].c[1], r2 = gk * dxs - rig[r].c[2];
-                val[0] = d0; val[1] = d1; val[2] = d2;
-                val[3] = r1 * d2 - r2 * d1;
-                val[4] = r2 * d0 - r0 * d2;
-                val[5] = r0 * d1 - r1 * d0;
-            }
-#pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                float x = val[c];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-                if (lane == 0) atomicAdd(&simp[r * 6 + c], x);
-            }
-        }
-        __syncthreads();
     }
-    if (s_scene >= 0) {
-        for (int t = tid; t < s_nrig * 6; t += kGridThreads)
-            if (simp[t] != 0.f) atomicAdd(&a.impulse[s_scene * kMaxRigids * 6 + t], (double)simp[t]);
-    }
+    __syncthreads();
+    if (s_staged >= 0) flush_impulse(a, simp, s_staged, s_nrig, tid);
 }
 
 // ------------------------------------------------------------------ G2P
+//
+// One CTA per active particle brick.  The 2x2x2 node bricks holding the 6^3
+// velocity window are staged in shared memory by bulk-copy TMA, double
+// buffered: the next brick's window is in flight while this brick computes.
+
+__device__ __forceinline__ void issue_halo(const StepArgs& a, int item, float4* dst, unsigned long long* bar)
+{
+    const int b = a.sb.act_brick[item];
+    const SceneDev& sc = a.scenes[a.sb.act_scene[item]];
+    const int nb = sc.nb, lb = b - sc.brick_base;
+    const int bx = lb / (nb * nb), by = (lb / nb) % nb, bz = lb % nb;
+    fence_proxy_async();
+    unsigned bytes = 0;
+#pragma unroll
+    for (int o = 0; o < 8; ++o)
+        if (bx + (o >> 2) < nb && by + ((o >> 1) & 1) < nb && bz + (o & 1) < nb) bytes += 64 * sizeof(float4);
+    mbar_expect_tx(bar, bytes);
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+        const int ex = bx + (o >> 2), ey = by + ((o >> 1) & 1), ez = bz + (o & 1);
+        if (ex < nb && ey < nb && ez < nb)
+            bulk_g2s(dst + o * 64, &a.V[(sc.brick_base + (ex * nb + ey) * nb + ez) * 64], 64 * sizeof(float4), bar);
+    }
+}
 
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_g2p(StepArgs a)
+__global__ void __launch_bounds__(BLOCK, 768 / BLOCK) k_g2p(StepArgs a)
 {
-    __shared__ __align__(128) float4 vw[8 * 64];
-    __shared__ __align__(8) unsigned long long bar;
-    __shared__ int s_item;
+    __shared__ __align__(128) float4 vw[2][8 * 64];
+    __shared__ __align__(8) unsigned long long bar[2];
+    __shared__ int s_item[2];
     const int tid = threadIdx.x;
     const int cap = a.cap;
+    const int n_act = a.sb.counters[CTR_N_ACT];
     if (tid == 0) {
-        mbar_init(&bar, 1);
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
         fence_mbar_init();
+        const int first = atomicAdd(&a.sb.counters[CTR_WORK_G2P], 1);
+        s_item[0] = first;
+        if (first < n_act) issue_halo(a, first, vw[0], &bar[0]);
     }
     if (blockIdx.x == 0) {
         // scene clocks advance once per substep (read by the next grid update)
@@ -690,61 +839,42 @@ __global__ void __launch_bounds__(BLOCK) k_g2p(StepArgs a)
         }
     }
     __syncthreads();
-    unsigned phase = 0;
-    const int n_act = a.sb.counters[CTR_N_ACT];
+    unsigned phase[2] = {0u, 0u};
+    int buf = 0;
     for (;;) {
-        if (tid == 0) s_item = atomicAdd(&a.sb.counters[CTR_WORK_G2P], 1);
-        __syncthreads();
-        const int item = s_item;
+        const int item = s_item[buf];
         if (item >= n_act) break;
+        if (tid == 0) {
+            // prefetch the next brick's window into the other buffer (free: the
+            // barrier at the end of the previous iteration retired its readers)
+            const int next = atomicAdd(&a.sb.counters[CTR_WORK_G2P], 1);
+            s_item[buf ^ 1] = next;
+            if (next < n_act) issue_halo(a, next, vw[buf ^ 1], &bar[buf ^ 1]);
+        }
+        const bool ok = mbar_wait_bounded(&bar[buf], phase[buf]);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicOr(&a.err[a.sb.act_scene[item]], MPM_EBIT_TIMEOUT);
+            mbar_wait_bounded(&bar[buf], phase[buf]);  // let copies in flight land before leaving
+            mbar_wait_bounded(&bar[buf ^ 1], phase[buf ^ 1]);
+            return;
+        }
+        phase[buf] ^= 1u;
         const int b = a.sb.act_brick[item], start = a.sb.act_start[item], count = a.sb.act_count[item];
         const int scene = a.sb.act_scene[item];
         const SceneDev sc = a.scenes[scene];
         const int n = sc.n, nb = sc.nb, lb = b - sc.brick_base;
-        const int bx = lb / (nb * nb), by = (lb / nb) % nb, bz = lb % nb;
-        if (tid == 0) {
-            // stage the 2x2x2 node bricks (b + {0,1}^3) holding the 6^3 window
-            fence_proxy_async();
-            unsigned bytes = 0;
-#pragma unroll
-            for (int o = 0; o < 8; ++o)
-                if (bx + (o >> 2) < nb && by + ((o >> 1) & 1) < nb && bz + (o & 1) < nb) bytes += 64 * sizeof(float4);
-            mbar_expect_tx(&bar, bytes);
-#pragma unroll
-            for (int o = 0; o < 8; ++o) {
-                const int cx = bx + (o >> 2), cy = by + ((o >> 1) & 1), cz = bz + (o & 1);
-                if (cx < nb && cy < nb && cz < nb) {
-                    const int nbk = sc.brick_base + (cx * nb + cy) * nb + cz;
-                    bulk_g2s(&vw[o * 64], &a.V[nbk * 64], 64 * sizeof(float4), &bar);
-                }
-            }
-        }
-        const bool ok = mbar_wait_bounded(&bar, phase);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) atomicOr(&a.err[scene], MPM_EBIT_TIMEOUT);
-            mbar_wait_bounded(&bar, phase);  // let copies in flight land before leaving
-            return;
-        }
-        phase ^= 1u;
+        const int ox = (lb / (nb * nb)) * 4, oy = ((lb / nb) % nb) * 4, oz = (lb % nb) * 4;
         const float fn = (float)n, dt = a.dt;
-        const int ox = bx * 4, oy = by * 4, oz = bz * 4;
+        const float4* win = vw[buf];
         unsigned ebits = 0;
         for (int k0 = 0; k0 < count; k0 += BLOCK) {
             const int k = k0 + tid;
             const bool valid = k < count;
             int key = 0;
-            unsigned ood = 0;
-            float xn[3], vp[3], Cn[9], Fn[9], mu = 0.f, lam = 0.f;
-            int pid = 0;
             if (valid) {
                 const int p = a.sb.perm[start + k];
+                const int s = start + k;
                 const float x0 = a.in.x[p], x1 = a.in.x[cap + p], x2 = a.in.x[2 * cap + p];
-                float F[9];
-#pragma unroll
-                for (int i = 0; i < 9; ++i) F[i] = a.in.F[i * cap + p];
-                pid = a.in.id[p];
-                if (sc.pp_mat) { mu = a.in.mu[p]; lam = a.in.lam[p]; }
-                else { mu = sc.mu; lam = sc.lam; }
                 int b0, b1, b2;
                 base_cell(x0, n, b0);
                 base_cell(x1, n, b1);
@@ -772,7 +902,7 @@ __global__ void __launch_bounds__(BLOCK) k_g2p(StepArgs a)
                         for (int k2 = 0; k2 < 3; ++k2) {
                             const int wk = l2 + k2;
                             const int sub = ((wi >> 2) << 2) | ((wj >> 2) << 1) | (wk >> 2);
-                            const float4 g = vw[sub * 64 + (wi & 3) * 16 + (wj & 3) * 4 + (wk & 3)];
+                            const float4 g = win[sub * 64 + (wi & 3) * 16 + (wj & 3) * 4 + (wk & 3)];
                             const float W = wij * w2[k2];
                             const float g0 = W * g.x, g1 = W * g.y, g2 = W * g.z;
                             v0 += g0; v1 += g1; v2 += g2;
@@ -783,48 +913,62 @@ __global__ void __launch_bounds__(BLOCK) k_g2p(StepArgs a)
                         }
                     }
                 }
-                // C = D^-1 sum N v (x_I - x_p)^T = 4/dx^2 * dx * B  (Eq. 9)
+                // C = D^-1 sum N v (x_I - x_p)^T = 4/dx^2 * dx * B  (Eq. 9); x += dt v (Eq. 4)
                 const float c4 = 4.0f * fn;
 #pragma unroll
-                for (int i = 0; i < 9; ++i) Cn[i] = c4 * B[i];
-                vp[0] = v0; vp[1] = v1; vp[2] = v2;
-                xn[0] = x0 + dt * v0;
-                xn[1] = x1 + dt * v1;
-                xn[2] = x2 + dt * v2;
+                for (int i = 0; i < 9; ++i) B[i] *= c4;
+                const float xn0 = x0 + dt * v0, xn1 = x1 + dt * v1, xn2 = x2 + dt * v2;
+                a.out.x[s] = xn0; a.out.x[cap + s] = xn1; a.out.x[2 * cap + s] = xn2;
+                a.out.v[s] = v0; a.out.v[cap + s] = v1; a.out.v[2 * cap + s] = v2;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) a.out.C[(size_t)i * cap + s] = B[i];
+                a.out.id[s] = a.in.id[p];
+                float mu, lam;
+                if (sc.pp_mat) {
+                    mu = a.in.mu[p];
+                    lam = a.in.lam[p];
+                    a.out.mu[s] = mu;
+                    a.out.lam[s] = lam;
+                } else {
+                    mu = sc.mu;
+                    lam = sc.lam;
+                }
+                unsigned ood = 0;
+                key = brick_key(sc, xn0, xn1, xn2, ood);
                 // F <- (I + dt C) F  (Eq. 10)
+                float Fn[9];
 #pragma unroll
-                for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c) {
+                    const float F0 = a.in.F[(size_t)c * cap + p], F1 = a.in.F[(size_t)(3 + c) * cap + p],
+                                F2 = a.in.F[(size_t)(6 + c) * cap + p];
 #pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        Fn[3 * r + c] = F[3 * r + c] + dt * (Cn[3 * r] * F[c] + Cn[3 * r + 1] * F[3 + c] + Cn[3 * r + 2] * F[6 + c]);
-                if (a.plasticity) ebits |= von_mises(Fn, mu, a.yield_stress);
-                float chk = xn[0] + xn[1] + xn[2] + v0 + v1 + v2;
+                    for (int r = 0; r < 3; ++r) {
+                        const float Fr = r == 0 ? F0 : (r == 1 ? F1 : F2);
+                        Fn[3 * r + c] = Fr + dt * (B[3 * r] * F0 + B[3 * r + 1] * F1 + B[3 * r + 2] * F2);
+                    }
+                }
+                // plasticity and stress: the last step of the G2P loop (Algorithm 1)
+                float t6[6];
+                ebits |= constitutive(a.model, a.plasticity, a.yield_stress, mu, lam, Fn, t6);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) a.out.F[(size_t)i * cap + s] = Fn[i];
+#pragma unroll
+                for (int i = 0; i < 6; ++i) a.out.tau[(size_t)i * cap + s] = t6[i];
+                float chk = xn0 + xn1 + xn2 + v0 + v1 + v2;
 #pragma unroll
                 for (int i = 0; i < 9; ++i) chk += Fn[i];
                 if (!isfinite(chk)) ebits |= MPM_EBIT_NONFINITE;
-                key = brick_key(sc, xn[0], xn[1], xn[2], ood);
-                if (ood) ebits |= MPM_EBIT_OUT_OF_DOMAIN;
+                else if (ood) ebits |= MPM_EBIT_OUT_OF_DOMAIN;
             }
             const int rank = aggregated_rank(a.sb.cnt, key, valid);
             if (valid) {
-                const int s = start + k;
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    a.out.x[d * cap + s] = xn[d];
-                    a.out.v[d * cap + s] = vp[d];
-                }
-#pragma unroll
-                for (int i = 0; i < 9; ++i) a.out.C[i * cap + s] = Cn[i];
-#pragma unroll
-                for (int i = 0; i < 9; ++i) a.out.F[i * cap + s] = Fn[i];
-                if (sc.pp_mat) { a.out.mu[s] = mu; a.out.lam[s] = lam; }
-                a.out.id[s] = pid;
-                a.sb.key[s] = key;
-                a.sb.rank[s] = rank;
+                a.sb.key[start + k] = key;
+                a.sb.rank[start + k] = rank;
             }
         }
         if (ebits) atomicOr(&a.err[scene], ebits);
         __syncthreads();
+        buf ^= 1;
     }
 }
 
@@ -896,10 +1040,10 @@ __global__ void k_read_grid(const float4* V, const int* brick_epoch, const int* 
 
 static int n_blocks(long long n, int t) { return (int)((n + t - 1) / t); }
 
-cudaError_t launch_init_keys(const StepArgs& a, const PState& st, cudaStream_t s)
+cudaError_t launch_prepare(const StepArgs& a, const PState& st, cudaStream_t s)
 {
     if (a.r.np == 0) return cudaSuccess;
-    k_init_keys<<<n_blocks(a.r.np, 256), 256, 0, s>>>(a, st);
+    k_prepare<<<n_blocks(a.r.np, 256), 256, 0, s>>>(a, st);
     return cudaGetLastError();
 }
 
@@ -916,17 +1060,14 @@ cudaError_t launch_sort(const StepArgs& a, cudaStream_t s)
 
 cudaError_t launch_p2g(const StepArgs& a, cudaStream_t s)
 {
-    switch (a.p2g_threads) {
-    case 128: k_p2g<128><<<a.persistent_ctas, 128, 0, s>>>(a); break;
-    case 512: k_p2g<512><<<a.persistent_ctas, 512, 0, s>>>(a); break;
-    default: k_p2g<256><<<a.persistent_ctas, 256, 0, s>>>(a); break;
-    }
+    if (a.p2g_chunk == 2 * kP2GThreads) k_p2g<2 * kP2GThreads><<<a.p2g_ctas, kP2GThreads, 0, s>>>(a);
+    else k_p2g<kP2GThreads><<<a.p2g_ctas, kP2GThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_grid(const StepArgs& a, cudaStream_t s)
 {
-    k_grid<<<a.persistent_ctas * 4, kGridThreads, 0, s>>>(a);
+    k_grid<<<a.grid_ctas, kGridThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -970,12 +1111,11 @@ cudaError_t launch_read_grid(const float4* V, const int* brick_epoch, const int*
     return cudaGetLastError();
 }
 
-int occupancy_p2g(int threads)
+int occupancy_p2g(int chunk)
 {
     int b = 0;
-    if (threads == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_p2g<128>, 128, 0);
-    else if (threads == 512) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_p2g<512>, 512, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_p2g<256>, 256, 0);
+    if (chunk == 2 * kP2GThreads) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_p2g<2 * kP2GThreads>, kP2GThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_p2g<kP2GThreads>, kP2GThreads, 0);
     return b;
 }
 

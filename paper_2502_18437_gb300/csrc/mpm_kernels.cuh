@@ -48,15 +48,18 @@ struct StepArgs {
     int bound, floor_sticky;
     int model, plasticity;
     float yield_stress;
-    int persistent_ctas;         // CTAs of the persistent kernels
-    int p2g_threads, g2p_threads;
+    int persistent_ctas;         // CTAs of the persistent G2P kernel
+    int p2g_ctas, grid_ctas;     // CTAs of the persistent P2G and grid kernels
+    int p2g_chunk, g2p_threads;
 };
 
+constexpr int kStateFloats = 32;  // x3 v3 C9 F9 tau6 mu lam (+ int id)
+constexpr int kP2GThreads = 192;  // 64 cells x 3 node slices
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
-cudaError_t launch_init_keys(const StepArgs& a, const PState& st, cudaStream_t s);
+cudaError_t launch_prepare(const StepArgs& a, const PState& st, cudaStream_t s);
 cudaError_t launch_sort(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_p2g(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_grid(const StepArgs& a, cudaStream_t s);
@@ -74,7 +77,7 @@ cudaError_t launch_scatter_field(const PState& st, int cap, int p0, int np, int 
                                  cudaStream_t s);
 cudaError_t launch_read_grid(const float4* V, const int* brick_epoch, const int* epoch, const SceneDev* scenes,
                              int scene, int n, int brick_base, float* dst, cudaStream_t s);
-int occupancy_p2g(int threads);
+int occupancy_p2g(int chunk);
 int occupancy_g2p(int threads);
 
 }  // namespace mpm

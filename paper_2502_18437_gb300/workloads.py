@@ -131,16 +131,19 @@ def tissue_slab(cells=(128, 16, 128), lo=(0.25, 0.03, 0.25), size=(0.5, 0.1, 0.5
     dx = 1.0 / n
     rigids = []
     if with_tools:
-        cx, cz = lo[0] + size[0] / 2, lo[2] + size[2] / 2
+        # centre line offset by a fraction of a cell so that no grid plane holds
+        # the blade's mid-plane or the thread's axis (contact decisions there are
+        # ties of the normal's sign)
+        cx, cz = lo[0] + size[0] / 2 + 0.37 * dx, lo[2] + size[2] / 2 + 0.21 * dx
         top = lo[1] + size[1]
-        half_edge, half_depth = 0.3 * size[2], 0.08 * size[1] / 0.1 / 2
+        half_edge, half_depth = 0.3 * size[2], 0.04
         edge_y = top - 0.01
         rigids.append(quad_slicer((cx, edge_y + half_depth, cz), BLADE_EDGE_Z_DOWN, half_edge=half_edge,
                                   half_depth=half_depth, thickness=0.002, vel=(0.0, -0.1, 0.0),
                                   mu_k=0.3, c_d=1.0, margin=dx))
         L = 0.8 * size[0]
         pts = np.stack([np.linspace(-L / 2, L / 2, 33), np.zeros(33), np.zeros(33)], -1)
-        rigids.append(segments((cx, lo[1] + 0.5 * size[1], cz), (1, 0, 0, 0), pts, radius=0.003,
+        rigids.append(segments((cx, lo[1] + 0.5 * size[1] + 0.29 * dx, cz), (1, 0, 0, 0), pts, radius=0.003,
                                vel=(0.05, 0.0, 0.0), mu_k=0.3, c_d=1.0, margin=dx))
     return _scene(n, x, np.zeros((N, 3)), E, 0.4, rho=1000.0, V0=V0, model="neo_hookean", dt=dt,
                   substeps=substeps, rigids=rigids, name=f"tissue_slab_{N}p_n{n}")
