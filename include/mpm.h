@@ -51,12 +51,14 @@ extern "C" {
 #define MPM_ERR_CAPACITY (-7)         /* more particles than max_particles       */
 #define MPM_ERR_TIMEOUT (-8)          /* a bounded wait ran out                  */
 #define MPM_ERR_STATE (-9)            /* call out of order (e.g. no tape recorded) */
+#define MPM_ERR_INTERNAL (-10)        /* a device-side consistency check failed      */
 
 /* device error bits reported by mpm_get_error */
 #define MPM_EBIT_OUT_OF_DOMAIN 1u
 #define MPM_EBIT_NONFINITE 2u
 #define MPM_EBIT_INVERTED 4u
 #define MPM_EBIT_TIMEOUT 8u
+#define MPM_EBIT_INTERNAL 16u /* sort bookkeeping inconsistent: the substep's work was skipped */
 
 /* ---- enumerations ---------------------------------------------------- */
 enum { MPM_MEM_HOST = 0, MPM_MEM_DEVICE = 1 };
@@ -89,7 +91,9 @@ enum {
     MPM_OPT_GRAPH_CHUNK = 6,    /* substeps captured per graph (1..64)              */
     MPM_OPT_PHASE_TIMING = 7,   /* 0/1: record CUDA events around each phase of every
                                    substep (forces direct launches); see mpm_phase_stats */
-    MPM_OPT_P2G_CHUNK = 8       /* particles staged per pass of the P2G kernel: 192/384 */
+    MPM_OPT_P2G_CHUNK = 8,      /* particles staged per pass of the P2G kernel: 192/384 */
+    MPM_OPT_FUSED = 9           /* 1: fuse each substep's G2P with the next substep's
+                                   P2G; 0 (default): separate P2G and G2P kernels */
 };
 
 /* ---- configuration --------------------------------------------------- */
@@ -223,7 +227,9 @@ int mpm_scene_count(mpm_ctx* ctx, int scene, int64_t* count);
 /* Measurement hook (no counterpart in the paper).  Waits (bounded) for the
  * stream, then reports, for the substeps run since the last reset with
  * MPM_OPT_PHASE_TIMING on, the summed device time in milliseconds of each
- * phase: ms[0] sort (scan + scatter), ms[1] P2G, ms[2] grid update, ms[3] G2P;
+ * phase: ms[0] sort (scan + scatter), ms[1] P2G (zero for fused substeps that
+ * reuse the previous substep's scatter), ms[2] grid update, ms[3] G2P or the
+ * fused G2P + P2G;
  * *n_substeps the number of substeps timed; active[0] / active[1] the numbers
  * of active particle bricks / node bricks of the last substep (all scenes of
  * the last launch group).  reset != 0 clears the sums after reading.

@@ -56,10 +56,9 @@ PState state_view(float* base, int cap)
     s.v = base + 3 * (size_t)cap;
     s.C = base + 6 * (size_t)cap;
     s.F = base + 15 * (size_t)cap;
-    s.tau = base + 24 * (size_t)cap;
-    s.mu = base + 30 * (size_t)cap;
-    s.lam = base + 31 * (size_t)cap;
-    s.id = reinterpret_cast<int*>(base + 32 * (size_t)cap);
+    s.mu = base + 24 * (size_t)cap;
+    s.lam = base + 25 * (size_t)cap;
+    s.id = reinterpret_cast<int*>(base + 26 * (size_t)cap);
     return s;
 }
 
@@ -156,13 +155,17 @@ StepArgs step_args(mpm_ctx* c, float dt, int s0, int s1, const PState& in, const
     a.persistent_ctas = c->num_sms * cap_occ(c, occupancy_g2p(c->g2p_threads));
     a.p2g_ctas = c->num_sms * cap_occ(c, occupancy_p2g(c->p2g_chunk));
     a.grid_ctas = c->num_sms * 8;
+    a.fused_ctas = c->num_sms * cap_occ(c, occupancy_g2p2g());
     a.p2g_chunk = c->p2g_chunk;
     a.g2p_threads = c->g2p_threads;
     return a;
 }
 
-// One substep of every scene: sort, P2G, grid update, G2P.
-int enqueue_substep(mpm_ctx* c, float dt, const PState& in, const PState& out)
+// One substep of every scene.  Unfused: sort, P2G, grid update, G2P.  Fused
+// (default): sort, P2G only when G does not already hold this state's P2G
+// (need_p2g), grid update, then the fused G2P + P2G, which leaves the next
+// substep's P2G in G.
+int enqueue_substep(mpm_ctx* c, float dt, const PState& in, const PState& out, bool need_p2g)
 {
     const int groups = c->launch_mode == 1 ? c->n_scenes : 1;
     for (int g = 0; g < groups; ++g) {
@@ -184,13 +187,21 @@ int enqueue_substep(mpm_ctx* c, float dt, const PState& in, const PState& out)
         if (ev) MPM_CK(cudaEventRecord(ev[0], c->stream));
         MPM_CK(launch_sort(a, c->stream));
         if (ev) MPM_CK(cudaEventRecord(ev[1], c->stream));
-        MPM_CK(launch_p2g(a, c->stream));
+        if (!c->fused || need_p2g) MPM_CK(launch_p2g(a, c->stream));
         if (ev) MPM_CK(cudaEventRecord(ev[2], c->stream));
         MPM_CK(launch_grid(a, c->stream));
         if (ev) MPM_CK(cudaEventRecord(ev[3], c->stream));
-        MPM_CK(launch_g2p(a, c->stream));
+        if (c->fused) MPM_CK(launch_g2p2g(a, c->stream));
+        else MPM_CK(launch_g2p(a, c->stream));
         if (ev) MPM_CK(cudaEventRecord(ev[4], c->stream));
     }
+    return MPM_OK;
+}
+
+// The state or dt changed: G's pending scatter no longer applies.
+int invalidate_pending(mpm_ctx* c)
+{
+    c->g_pending = false;
     return MPM_OK;
 }
 
@@ -221,6 +232,7 @@ extern "C" const char* mpm_status_string(int s)
     case MPM_ERR_CAPACITY: return "particle capacity exceeded";
     case MPM_ERR_TIMEOUT: return "bounded wait timed out";
     case MPM_ERR_STATE: return "call out of order";
+    case MPM_ERR_INTERNAL: return "device-side consistency check failed";
     default: return "unknown status";
     }
 }
@@ -382,6 +394,10 @@ extern "C" int mpm_set_option(mpm_ctx* c, int option, int64_t value)
         c->graph_chunk = (int)value;
         break;
     case MPM_OPT_PHASE_TIMING: c->phase_timing = value != 0; break;
+    case MPM_OPT_FUSED:
+        c->fused = value != 0;
+        invalidate_pending(c);
+        break;
     default: return MPM_ERR_INVALID_ARGUMENT;
     }
     clear_graphs(c);
@@ -481,6 +497,7 @@ extern "C" int mpm_add_particles(mpm_ctx* c, int scene, int64_t n, const float* 
     c->total_particles += (int)n;
     c->scenes_dirty = true;
     c->keys_valid = false;
+    invalidate_pending(c);
     clear_graphs(c);
     st = upload_scenes(c);
     if (st) return st;
@@ -559,15 +576,27 @@ extern "C" int mpm_substep(mpm_ctx* c, float dt, int n_substeps)
             if ((st = mpm_tape_record_substep(c, dt))) return st;
         return MPM_OK;
     }
+    int left = n_substeps;
+    const bool pending = c->fused && c->g_pending && c->g_dt == dt;
+    if (!pending) {
+        // a fresh P2G: clear whatever scatter G still holds, then one direct substep
+        if (c->g_dirty) MPM_CK(cudaMemsetAsync(c->G, 0, sizeof(float4) * (size_t)c->total_bricks * 64, c->stream));
+        if ((st = enqueue_substep(c, dt, c->st[c->cur], c->st[c->cur ^ 1], true))) return st;
+        c->cur ^= 1;
+        c->h_time += (double)dt;
+        --left;
+    }
+    c->g_pending = c->fused != 0;
+    c->g_dirty = c->fused != 0;
+    c->g_dt = dt;
     if (!c->use_graphs || c->phase_timing) {
-        for (int k = 0; k < n_substeps; ++k) {
-            if ((st = enqueue_substep(c, dt, c->st[c->cur], c->st[c->cur ^ 1]))) return st;
+        for (int k = 0; k < left; ++k) {
+            if ((st = enqueue_substep(c, dt, c->st[c->cur], c->st[c->cur ^ 1], false))) return st;
             c->cur ^= 1;
             c->h_time += (double)dt;
         }
         return MPM_OK;
     }
-    int left = n_substeps;
     while (left > 0) {
         const int L = left >= c->graph_chunk ? c->graph_chunk : 1;
         auto key = std::make_tuple(float_bits(dt), L, c->cur);
@@ -578,7 +607,7 @@ extern "C" int mpm_substep(mpm_ctx* c, float dt, int n_substeps)
             int cur = c->cur;
             int err = MPM_OK;
             for (int k = 0; k < L && !err; ++k) {
-                err = enqueue_substep(c, dt, c->st[cur], c->st[cur ^ 1]);
+                err = enqueue_substep(c, dt, c->st[cur], c->st[cur ^ 1], false);
                 cur ^= 1;
             }
             cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
@@ -605,6 +634,7 @@ static int error_status(unsigned bits)
     if (bits & MPM_EBIT_OUT_OF_DOMAIN) return MPM_ERR_OUT_OF_DOMAIN;
     if (bits & MPM_EBIT_INVERTED) return MPM_ERR_INVERTED;
     if (bits & MPM_EBIT_TIMEOUT) return MPM_ERR_TIMEOUT;
+    if (bits & MPM_EBIT_INTERNAL) return MPM_ERR_INTERNAL;
     return MPM_OK;
 }
 
@@ -709,8 +739,9 @@ extern "C" int mpm_write_state(mpm_ctx* c, int scene, uint32_t fields, const voi
         off += align256(bytes);
         MPM_CK(launch_scatter_field(cur, c->cap, sc.p_begin, np, f, static_cast<const float*>(d), c->stream));
     }
-    // new positions need new brick keys; a new F needs its stress
-    if (fields & (MPM_FIELD_X | MPM_FIELD_F)) c->keys_valid = false;
+    // new positions need new brick keys; any new field changes the pending P2G
+    if (fields & MPM_FIELD_X) c->keys_valid = false;
+    invalidate_pending(c);
     if (mem == MPM_MEM_HOST) return wait_stream(c);
     return MPM_OK;
 }
@@ -784,12 +815,13 @@ extern "C" int mpm_autotune(mpm_ctx* c, float dt, int trial_substeps, float* bes
                 c->p2g_chunk = chunks[a];
                 c->g2p_threads = threads[b];
                 c->ctas_per_sm = ctas[k];
-                // one untimed warm-up substep, then the timed trial
-                st = enqueue_substep(c, dt, c->st[c->cur], c->st[c->cur ^ 1]);
+                // one untimed warm-up substep from a clean accumulator, then the timed trial
+                ce = cudaMemsetAsync(c->G, 0, sizeof(float4) * nbk * 64, c->stream);
+                if (ce == cudaSuccess) st = enqueue_substep(c, dt, c->st[c->cur], c->st[c->cur ^ 1], true);
                 c->cur ^= 1;
-                if (!st) ce = cudaEventRecord(e0, c->stream);
+                if (!st && ce == cudaSuccess) ce = cudaEventRecord(e0, c->stream);
                 for (int s = 0; s < trial_substeps && !st && ce == cudaSuccess; ++s) {
-                    st = enqueue_substep(c, dt, c->st[c->cur], c->st[c->cur ^ 1]);
+                    st = enqueue_substep(c, dt, c->st[c->cur], c->st[c->cur ^ 1], false);
                     c->cur ^= 1;
                 }
                 if (!st && ce == cudaSuccess) ce = cudaEventRecord(e1, c->stream);
@@ -808,6 +840,9 @@ extern "C" int mpm_autotune(mpm_ctx* c, float dt, int trial_substeps, float* bes
             }
     if (ce == cudaSuccess && st == MPM_OK) st = wait_stream(c);
     c->cur = cur0;
+    // the trials left scatters in G that do not belong to the restored state
+    c->g_pending = false;
+    c->g_dirty = true;
     c->p2g_chunk = best[0];
     c->g2p_threads = best[1];
     c->ctas_per_sm = best[2];

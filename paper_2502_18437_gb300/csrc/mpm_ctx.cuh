@@ -47,6 +47,10 @@ struct mpm_ctx {
 
     bool keys_valid = false;
     bool scenes_dirty = true;
+    // fused substeps leave the next substep's P2G in G: valid for this state and dt
+    bool g_pending = false;
+    bool g_dirty = false;  // G may hold a pending scatter (must be cleared before a fresh P2G)
+    float g_dt = 0.f;
 
     // options
     int use_graphs = 1;
@@ -56,6 +60,7 @@ struct mpm_ctx {
     int ctas_per_sm = 0;
     int graph_chunk = 16;
     int phase_timing = 0;
+    int fused = 0;
     std::vector<cudaEvent_t> phase_events;  // 5 per timed substep
     size_t phase_used = 0;
     std::map<std::tuple<uint32_t, int, int>, cudaGraphExec_t> graphs;
@@ -70,7 +75,8 @@ namespace mpm {
 int status_from_cuda(cudaError_t e);
 int wait_stream(mpm_ctx* c);
 StepArgs step_args(mpm_ctx* c, float dt, int s0, int s1, const PState& in, const PState& out);
-int enqueue_substep(mpm_ctx* c, float dt, const PState& in, const PState& out);
+int enqueue_substep(mpm_ctx* c, float dt, const PState& in, const PState& out, bool need_p2g);
+int invalidate_pending(mpm_ctx* c);
 int ensure_keys(mpm_ctx* c);
 int upload_scenes(mpm_ctx* c);
 int ensure_stage(mpm_ctx* c, size_t bytes);

@@ -241,8 +241,15 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(StepArgs a)
             s_prefix = prefix;
             if (tile == n_tiles - 1) {
                 const int4 tot = add4(prefix, agg);
-                sb.counters[CTR_N_ACT] = tot.y;
-                sb.counters[CTR_N_NACT] = tot.z;
+                if (tot.x == a.r.np) {
+                    sb.counters[CTR_N_ACT] = tot.y;
+                    sb.counters[CTR_N_NACT] = tot.z;
+                } else {
+                    // histogram and particle count disagree: skip this substep's work
+                    sb.counters[CTR_N_ACT] = 0;
+                    sb.counters[CTR_N_NACT] = 0;
+                    atomicOr(&a.err[a.r.s0], MPM_EBIT_INTERNAL);
+                }
             }
         }
     }
@@ -274,7 +281,12 @@ __global__ void k_scatter(StepArgs a, int n_tiles)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = a.r.p0 + g;
-    if (g < a.r.np) a.sb.perm[__ldg(&a.sb.off[a.sb.key[i]]) + a.sb.rank[i]] = i;
+    if (g < a.r.np) {
+        const int key = a.sb.key[i];
+        const int dst = (key >= a.r.bb0 && key < a.r.bb0 + a.r.nbr) ? __ldg(&a.sb.off[key]) + a.sb.rank[i] : -1;
+        if (dst >= a.r.p0 && dst < a.r.p0 + a.r.np) a.sb.perm[dst] = i;
+        else atomicOr(&a.err[a.r.s0], MPM_EBIT_INTERNAL);
+    }
     if (g < n_tiles) a.sb.tile_status[g] = 0u;
     if (g == 0) a.sb.counters[CTR_TICKET] = 0;
 }
@@ -306,8 +318,8 @@ __device__ __forceinline__ int aggregated_rank(int* cnt, int key, bool valid)
     return rank;
 }
 
-// Keys, ranks and stresses of the stored particles after the host changed
-// positions or F (new particles, state writes).
+// Keys and ranks of the stored particles after the host changed positions
+// (new particles, state writes).
 __global__ void k_prepare(StepArgs a, PState st)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -327,13 +339,6 @@ __global__ void k_prepare(StepArgs a, PState st)
         unsigned ood = 0;
         key = brick_key(sc, st.x[i], st.x[a.cap + i], st.x[2 * a.cap + i], ood);
         if (ood) ebits |= MPM_EBIT_OUT_OF_DOMAIN;
-        float F[9], t6[6];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) F[k] = st.F[(size_t)k * a.cap + i];
-        const float mu = sc.pp_mat ? st.mu[i] : sc.mu, lam = sc.pp_mat ? st.lam[i] : sc.lam;
-        ebits |= constitutive(a.model, 0, 0.f, mu, lam, F, t6);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) st.tau[(size_t)k * a.cap + i] = t6[k];
     }
     const int rank = aggregated_rank(a.sb.cnt, key, valid);
     if (valid) {
@@ -343,21 +348,122 @@ __global__ void k_prepare(StepArgs a, PState st)
     }
 }
 
+// ------------------------------------------------------ transfer helpers
+
+constexpr int kRecFields = 21;  // w0[3] w1[3] w2[3] q[3] Ad[9]
+
+// Base cells, fractional offsets and quadratic B-spline weights of a position.
+__device__ __forceinline__ unsigned particle_weights(float x0, float x1, float x2, int n, int b[3], float f[3],
+                                                     float w[9])
+{
+    const float fn = (float)n;
+    const unsigned ood = base_cell(x0, n, b[0]) | base_cell(x1, n, b[1]) | base_cell(x2, n, b[2]);
+    f[0] = __fmaf_rn(x0, fn, -(float)b[0]);
+    f[1] = __fmaf_rn(x1, fn, -(float)b[1]);
+    f[2] = __fmaf_rn(x2, fn, -(float)b[2]);
+    bspline(f[0], w);
+    bspline(f[1], w + 3);
+    bspline(f[2], w + 6);
+    return ood ? MPM_EBIT_OUT_OF_DOMAIN : 0u;
+}
+
+// P2G coefficients (Eq. 8 with the APIC particle momentum, M^-1 = 4/dx^2 of
+// Eq. 7, V sigma = V0 tau): the momentum a particle gives node (i,j,k) of its
+// stencil is W_ijk (q + Ad (i,j,k)) with Ad = (m C - dt V0 M^-1 tau) dx and
+// q = m v - Ad f, so that Ad ((i,j,k) - f) = A (x_I - x_p).
+__device__ __forceinline__ void p2g_coeffs(float m, float kA, float dxs, const float v[3], const float C[9],
+                                           const float t6[6], const float f[3], float q[3], float Ad[9])
+{
+    const float tau[9] = {t6[0], t6[1], t6[2], t6[1], t6[3], t6[4], t6[2], t6[4], t6[5]};
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Ad[i] = (m * C[i] - kA * tau[i]) * dxs;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) q[r] = m * v[r] - (Ad[3 * r] * f[0] + Ad[3 * r + 1] * f[1] + Ad[3 * r + 2] * f[2]);
+}
+
+template <int N>
+__device__ __forceinline__ void put_record(float (*rec)[N], int k, const float w[9], const float q[3], const float Ad[9])
+{
+#pragma unroll
+    for (int i = 0; i < 9; ++i) rec[i][k] = w[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) rec[9 + i][k] = q[i];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) rec[12 + i][k] = Ad[i];
+}
+
+// Phase B of the per-cell accumulation: thread (cell, slice) adds the
+// contributions of the particles of its cell (order[beg..end)) to the 9 nodes
+// cell + (slice, j, k) in registers.
+template <int N>
+__device__ __forceinline__ void cell_accumulate(const float (*rec)[N], const short* order, int beg, int end, int slice,
+                                                float acc_w[9], float acc_p[9][3])
+{
+    const float si = (float)slice;
+    for (int j = beg; j < end; ++j) {
+        const int k = order[j];
+        const float wi = rec[slice][k];
+        const float wy[3] = {rec[3][k], rec[4][k], rec[5][k]};
+        const float wz[3] = {rec[6][k], rec[7][k], rec[8][k]};
+        // r(j,k) = q + Ad (slice, j, k)
+        const float r0 = rec[9][k] + si * rec[12][k], r1 = rec[10][k] + si * rec[15][k], r2 = rec[11][k] + si * rec[18][k];
+        const float a01 = rec[13][k], a11 = rec[16][k], a21 = rec[19][k];
+        const float a02 = rec[14][k], a12 = rec[17][k], a22 = rec[20][k];
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) {
+            const float wij = wi * wy[jj];
+            const float s0 = r0 + a01 * jj, s1 = r1 + a11 * jj, s2 = r2 + a21 * jj;
+#pragma unroll
+            for (int kk = 0; kk < 3; ++kk) {
+                const float W = wij * wz[kk];
+                const int q = jj * 3 + kk;
+                acc_w[q] += W;
+                acc_p[q][0] += W * (s0 + a02 * kk);
+                acc_p[q][1] += W * (s1 + a12 * kk);
+                acc_p[q][2] += W * (s2 + a22 * kk);
+            }
+        }
+    }
+}
+
+// Exclusive scan of the 64 per-cell counts by warp 0.
+__device__ __forceinline__ void scan_cells(const int* cell_cnt, int* cell_off, int tid)
+{
+    if (tid < 32) {
+        const int c_a = cell_cnt[2 * tid], c_b = cell_cnt[2 * tid + 1];
+        int incl = c_a + c_b;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, d);
+            if (tid >= d) incl += t;
+        }
+        const int excl = incl - c_a - c_b;
+        cell_off[2 * tid] = excl;
+        cell_off[2 * tid + 1] = excl + c_a;
+        if (tid == 31) cell_off[64] = incl;
+    }
+}
+
+// Global node index of node (gi, gj, gk) of a scene (brick layout).
+__device__ __forceinline__ int node_index(const SceneDev& sc, int gi, int gj, int gk)
+{
+    const int brick = sc.brick_base + ((gi >> 2) * sc.nb + (gj >> 2)) * sc.nb + (gk >> 2);
+    return brick * 64 + (gi & 3) * 16 + (gj & 3) * 4 + (gk & 3);
+}
+
 // ------------------------------------------------------------------ P2G
 //
 // One CTA per active particle brick (4^3 cells, a 6^3-node window).  Per chunk
-// of up to kP2GChunk particles:
-//   A. one thread per particle: weights, A_p = m C_p - dt V0 M^-1 tau_p
-//      (Eq. 8, M^-1 = 4/dx^2 of Eq. 7) folded into a per-particle record in
-//      shared memory; the chunk is counting-sorted by cell (64 bins);
+// of up to CHUNK particles:
+//   A. one thread per particle: stress, weights and P2G coefficients into a
+//      record in shared memory; the chunk is counting-sorted by cell;
 //   B. thread (cell c, slice i) sums, in registers, the contributions of the
 //      particles of cell c to its 9 nodes c + (i, j, k): no atomics.
 // At the end of the brick every thread adds its 9 node sums into the shared
 // window (the 32 lanes of a warp hold 32 distinct cells of one slice, so a
 // warp never hits the same node twice), and the window is added to HBM with
-// one vector reduction per node.
-
-constexpr int kRecFields = 21;  // w0[3] w1[3] w2[3] q[3] Ad[9]
+// one vector reduction per node.  Used for the first substep of a run (the
+// fused kernel below scatters every later substep).
 
 template <int CHUNK>
 __global__ void __launch_bounds__(kP2GThreads, CHUNK == kP2GThreads ? 5 : 4) k_p2g(StepArgs a)
@@ -382,7 +488,6 @@ __global__ void __launch_bounds__(kP2GThreads, CHUNK == kP2GThreads ? 5 : 4) k_p
         if (item >= n_act) break;
         const int b = a.sb.act_brick[item], start = a.sb.act_start[item], count = a.sb.act_count[item];
         const int scene = a.sb.act_scene[item];
-        if (tid == 0) a.sb.cnt[b] = 0;  // histogram of the next substep starts from zero
         const SceneDev sc = a.scenes[scene];
         const int n = sc.n, nb = sc.nb, lb = b - sc.brick_base;
         const int ox = (lb / (nb * nb)) * 4, oy = ((lb / nb) % nb) * 4, oz = (lb % nb) * 4;
@@ -403,86 +508,34 @@ __global__ void __launch_bounds__(kP2GThreads, CHUNK == kP2GThreads ? 5 : 4) k_p
                 my_cell[u] = -1;
                 if (k < cn) {
                     const int p = a.sb.perm[start + c0 + k];
-                    const float x0 = a.in.x[p], x1 = a.in.x[cap + p], x2 = a.in.x[2 * cap + p];
-                    int b0, b1, b2;
-                    ebits |= (base_cell(x0, n, b0) | base_cell(x1, n, b1) | base_cell(x2, n, b2)) ? MPM_EBIT_OUT_OF_DOMAIN : 0u;
-                    const float f0 = __fmaf_rn(x0, fn, -(float)b0);
-                    const float f1 = __fmaf_rn(x1, fn, -(float)b1);
-                    const float f2 = __fmaf_rn(x2, fn, -(float)b2);
-                    float w[3];
-                    bspline(f0, w);
-                    rec[0][k] = w[0]; rec[1][k] = w[1]; rec[2][k] = w[2];
-                    bspline(f1, w);
-                    rec[3][k] = w[0]; rec[4][k] = w[1]; rec[5][k] = w[2];
-                    bspline(f2, w);
-                    rec[6][k] = w[0]; rec[7][k] = w[1]; rec[8][k] = w[2];
-                    float t6[6];
+                    int bc[3];
+                    float f[3], w[9];
+                    ebits |= particle_weights(a.in.x[p], a.in.x[cap + p], a.in.x[2 * cap + p], n, bc, f, w);
+                    float F[9], C[9], v[3], t6[6];
 #pragma unroll
-                    for (int q = 0; q < 6; ++q) t6[q] = a.in.tau[(size_t)q * cap + p];
-                    const float tau[9] = {t6[0], t6[1], t6[2], t6[1], t6[3], t6[4], t6[2], t6[4], t6[5]};
-                    float Ad[9];
+                    for (int q = 0; q < 9; ++q) F[q] = a.in.F[(size_t)q * cap + p];
 #pragma unroll
-                    for (int q = 0; q < 9; ++q) Ad[q] = (m * a.in.C[(size_t)q * cap + p] - kA * tau[q]) * dxs;
+                    for (int q = 0; q < 9; ++q) C[q] = a.in.C[(size_t)q * cap + p];
 #pragma unroll
-                    for (int r = 0; r < 3; ++r) {
-                        const float vr = a.in.v[(size_t)r * cap + p];
-                        rec[9 + r][k] = m * vr - (Ad[3 * r] * f0 + Ad[3 * r + 1] * f1 + Ad[3 * r + 2] * f2);
-                    }
-#pragma unroll
-                    for (int q = 0; q < 9; ++q) rec[12 + q][k] = Ad[q];
-                    const int l0 = min(max(b0 - ox, 0), 3), l1 = min(max(b1 - oy, 0), 3), l2 = min(max(b2 - oz, 0), 3);
+                    for (int q = 0; q < 3; ++q) v[q] = a.in.v[(size_t)q * cap + p];
+                    const float mu = sc.pp_mat ? a.in.mu[p] : sc.mu, lam = sc.pp_mat ? a.in.lam[p] : sc.lam;
+                    ebits |= constitutive(a.model, 0, 0.f, mu, lam, F, t6);  // stress of the current F
+                    float q3[3], Ad[9];
+                    p2g_coeffs(m, kA, dxs, v, C, t6, f, q3, Ad);
+                    put_record<CHUNK>(rec, k, w, q3, Ad);
+                    const int l0 = min(max(bc[0] - ox, 0), 3), l1 = min(max(bc[1] - oy, 0), 3), l2 = min(max(bc[2] - oz, 0), 3);
                     my_cell[u] = (l0 * 4 + l1) * 4 + l2;
                     my_rank[u] = atomicAdd(&cell_cnt[my_cell[u]], 1);
                 }
             }
             __syncthreads();
-            if (tid < 32) {
-                // exclusive scan of the 64 cell counts (2 per lane)
-                const int c_a = cell_cnt[2 * tid], c_b = cell_cnt[2 * tid + 1];
-                int incl = c_a + c_b;
-#pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const int t = __shfl_up_sync(kFull, incl, d);
-                    if (tid >= d) incl += t;
-                }
-                const int excl = incl - c_a - c_b;
-                cell_off[2 * tid] = excl;
-                cell_off[2 * tid + 1] = excl + c_a;
-                if (tid == 31) cell_off[64] = incl;
-            }
+            scan_cells(cell_cnt, cell_off, tid);
             __syncthreads();
 #pragma unroll
             for (int u = 0; u < PER; ++u)
                 if (my_cell[u] >= 0) order[cell_off[my_cell[u]] + my_rank[u]] = (short)(tid + u * kP2GThreads);
             __syncthreads();
-            // phase B: contributions of cell `cell` to nodes cell + (slice, j, k)
-            const int beg = cell_off[cell], end = cell_off[cell + 1];
-            for (int j = beg; j < end; ++j) {
-                const int k = order[j];
-                const float wi = rec[slice][k];
-                const float wy0 = rec[3][k], wy1 = rec[4][k], wy2 = rec[5][k];
-                const float wz0 = rec[6][k], wz1 = rec[7][k], wz2 = rec[8][k];
-                const float si = (float)slice;
-                // r(j,k) = q + Ad (slice, j, k)
-                const float r0 = rec[9][k] + si * rec[12][k], r1 = rec[10][k] + si * rec[15][k], r2 = rec[11][k] + si * rec[18][k];
-                const float a01 = rec[13][k], a11 = rec[16][k], a21 = rec[19][k];
-                const float a02 = rec[14][k], a12 = rec[17][k], a22 = rec[20][k];
-                const float wy[3] = {wy0, wy1, wy2}, wz[3] = {wz0, wz1, wz2};
-#pragma unroll
-                for (int jj = 0; jj < 3; ++jj) {
-                    const float wij = wi * wy[jj];
-                    const float s0 = r0 + a01 * jj, s1 = r1 + a11 * jj, s2 = r2 + a21 * jj;
-#pragma unroll
-                    for (int kk = 0; kk < 3; ++kk) {
-                        const float W = wij * wz[kk];
-                        const int q = jj * 3 + kk;
-                        acc_w[q] += W;
-                        acc_p[q][0] += W * (s0 + a02 * kk);
-                        acc_p[q][1] += W * (s1 + a12 * kk);
-                        acc_p[q][2] += W * (s2 + a22 * kk);
-                    }
-                }
-            }
+            cell_accumulate<CHUNK>(rec, order, cell_off[cell], cell_off[cell + 1], slice, acc_w, acc_p);
             __syncthreads();
             if (tid < 64) cell_cnt[tid] = 0;
             __syncthreads();
@@ -504,8 +557,7 @@ __global__ void __launch_bounds__(kP2GThreads, CHUNK == kP2GThreads ? 5 : 4) k_p
             if (mm == 0.0f) continue;
             const int gi = ox + t / 36, gj = oy + (t / 6) % 6, gk = oz + t % 6;
             if (gi >= n || gj >= n || gk >= n) continue;
-            const int brick = sc.brick_base + ((gi >> 2) * nb + (gj >> 2)) * nb + (gk >> 2);
-            red_add_v4(&a.G[brick * 64 + (gi & 3) * 16 + (gj & 3) * 4 + (gk & 3)], mm, win[1][t], win[2][t], win[3][t]);
+            red_add_v4(&a.G[node_index(sc, gi, gj, gk)], mm, win[1][t], win[2][t], win[3][t]);
         }
         if (ebits) atomicOr(&a.err[scene], ebits);
         __syncthreads();
@@ -756,7 +808,12 @@ __global__ void __launch_bounds__(kGridThreads) k_grid(StepArgs a)
                     if (gk > hi) v.z = fminf(v.z, 0.f);
                 }
                 a.V[node] = make_float4(v.x, v.y, v.z, g.x);
-                if (nid == 0) a.brick_epoch[B] = a.epoch[target];
+                if (nid == 0) {
+                    a.brick_epoch[B] = a.epoch[target];
+                    // the histogram of the next substep starts from zero (the scan
+                    // has read it; every non-empty brick is an active node brick)
+                    a.sb.cnt[B] = 0;
+                }
                 // impulse on each rigid: -(node momentum change), linear and angular
                 for (int r = 0; r < nr; ++r) {
                     const bool on = (touched >> r) & 1u;
@@ -814,20 +871,110 @@ __device__ __forceinline__ void issue_halo(const StepArgs& a, int item, float4* 
     }
 }
 
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 768 / BLOCK) k_g2p(StepArgs a)
+// G2P of one particle from the staged window (Eq. 4, Eq. 9, Eq. 10) followed by
+// the constitutive update (the last step of the G2P loop in Algorithm 1).
+// Writes x, v, C, F (and id, mu, lam) to slot s of the output state; returns
+// the new position, velocity, C and the Kirchhoff stress of the new F.
+struct G2POut {
+    float x[3], v[3], C[9], t6[6];
+};
+
+__device__ __forceinline__ unsigned g2p_particle(const StepArgs& a, const SceneDev& sc, const float4* win, int p, int s,
+                                                 int ox, int oy, int oz, G2POut& o)
 {
-    __shared__ __align__(128) float4 vw[2][8 * 64];
-    __shared__ __align__(8) unsigned long long bar[2];
-    __shared__ int s_item[2];
+    const int cap = a.cap, n = sc.n;
+    const float fn = (float)n, dt = a.dt;
+    unsigned ebits = 0;
+    const float x0 = a.in.x[p], x1 = a.in.x[cap + p], x2 = a.in.x[2 * cap + p];
+    int bc[3];
+    float f[3], w[9];
+    particle_weights(x0, x1, x2, n, bc, f, w);
+    const int l0 = min(max(bc[0] - ox, 0), 3), l1 = min(max(bc[1] - oy, 0), 3), l2 = min(max(bc[2] - oz, 0), 3);
+    float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+    float B[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) B[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int wi = l0 + i;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int wj = l1 + j;
+            const float wij = w[i] * w[3 + j];
+#pragma unroll
+            for (int k2 = 0; k2 < 3; ++k2) {
+                const int wk = l2 + k2;
+                const int sub = ((wi >> 2) << 2) | ((wj >> 2) << 1) | (wk >> 2);
+                const float4 g = win[sub * 64 + (wi & 3) * 16 + (wj & 3) * 4 + (wk & 3)];
+                const float W = wij * w[6 + k2];
+                const float g0 = W * g.x, g1 = W * g.y, g2 = W * g.z;
+                v0 += g0; v1 += g1; v2 += g2;
+                const float d0 = (float)i - f[0], d1 = (float)j - f[1], d2 = (float)k2 - f[2];
+                B[0] += g0 * d0; B[1] += g0 * d1; B[2] += g0 * d2;
+                B[3] += g1 * d0; B[4] += g1 * d1; B[5] += g1 * d2;
+                B[6] += g2 * d0; B[7] += g2 * d1; B[8] += g2 * d2;
+            }
+        }
+    }
+    // C = D^-1 sum N v (x_I - x_p)^T = 4/dx^2 * dx * B  (Eq. 9); x += dt v (Eq. 4)
+    const float c4 = 4.0f * fn;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) o.C[i] = B[i] * c4;
+    o.v[0] = v0; o.v[1] = v1; o.v[2] = v2;
+    o.x[0] = x0 + dt * v0;
+    o.x[1] = x1 + dt * v1;
+    o.x[2] = x2 + dt * v2;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        a.out.x[(size_t)d * cap + s] = o.x[d];
+        a.out.v[(size_t)d * cap + s] = o.v[d];
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) a.out.C[(size_t)i * cap + s] = o.C[i];
+    a.out.id[s] = a.in.id[p];
+    float mu, lam;
+    if (sc.pp_mat) {
+        mu = a.in.mu[p];
+        lam = a.in.lam[p];
+        a.out.mu[s] = mu;
+        a.out.lam[s] = lam;
+    } else {
+        mu = sc.mu;
+        lam = sc.lam;
+    }
+    // F <- (I + dt C) F  (Eq. 10)
+    float Fn[9];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float F0 = a.in.F[(size_t)c * cap + p], F1 = a.in.F[(size_t)(3 + c) * cap + p],
+                    F2 = a.in.F[(size_t)(6 + c) * cap + p];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const float Fr = r == 0 ? F0 : (r == 1 ? F1 : F2);
+            Fn[3 * r + c] = Fr + dt * (o.C[3 * r] * F0 + o.C[3 * r + 1] * F1 + o.C[3 * r + 2] * F2);
+        }
+    }
+    ebits |= constitutive(a.model, a.plasticity, a.yield_stress, mu, lam, Fn, o.t6);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) a.out.F[(size_t)i * cap + s] = Fn[i];
+    float chk = o.x[0] + o.x[1] + o.x[2] + v0 + v1 + v2;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) chk += Fn[i];
+    if (!isfinite(chk)) ebits |= MPM_EBIT_NONFINITE;
+    return ebits;
+}
+
+// Shared prologue of the brick-walking kernels: mbarriers, first halo, clocks.
+template <int BLOCK>
+__device__ __forceinline__ void walker_init(const StepArgs& a, int n_act, float4 (*vw)[8 * 64], unsigned long long* bar,
+                                            int* s_item, int* work)
+{
     const int tid = threadIdx.x;
-    const int cap = a.cap;
-    const int n_act = a.sb.counters[CTR_N_ACT];
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbar_init();
-        const int first = atomicAdd(&a.sb.counters[CTR_WORK_G2P], 1);
+        const int first = atomicAdd(work, 1);
         s_item[0] = first;
         if (first < n_act) issue_halo(a, first, vw[0], &bar[0]);
     }
@@ -839,132 +986,203 @@ __global__ void __launch_bounds__(BLOCK, 768 / BLOCK) k_g2p(StepArgs a)
         }
     }
     __syncthreads();
+}
+
+// Prefetch the next brick's halo and wait for this one; false on timeout (the
+// CTA must then return).
+__device__ __forceinline__ bool walker_next(const StepArgs& a, int n_act, float4 (*vw)[8 * 64], unsigned long long* bar,
+                                            int* s_item, int* work, int buf, unsigned* phase, int item)
+{
+    if (threadIdx.x == 0) {
+        const int next = atomicAdd(work, 1);
+        s_item[buf ^ 1] = next;
+        if (next < n_act) issue_halo(a, next, vw[buf ^ 1], &bar[buf ^ 1]);
+    }
+    const bool ok = mbar_wait_bounded(&bar[buf], phase[buf]);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) atomicOr(&a.err[a.sb.act_scene[item]], MPM_EBIT_TIMEOUT);
+        mbar_wait_bounded(&bar[buf], phase[buf]);  // let copies in flight land before leaving
+        mbar_wait_bounded(&bar[buf ^ 1], phase[buf ^ 1]);
+        return false;
+    }
+    phase[buf] ^= 1u;
+    return true;
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 768 / BLOCK) k_g2p(StepArgs a)
+{
+    __shared__ __align__(128) float4 vw[2][8 * 64];
+    __shared__ __align__(8) unsigned long long bar[2];
+    __shared__ int s_item[2];
+    const int tid = threadIdx.x;
+    const int n_act = a.sb.counters[CTR_N_ACT];
+    int* work = &a.sb.counters[CTR_WORK_G2P];
+    walker_init<BLOCK>(a, n_act, vw, bar, s_item, work);
     unsigned phase[2] = {0u, 0u};
     int buf = 0;
     for (;;) {
         const int item = s_item[buf];
         if (item >= n_act) break;
-        if (tid == 0) {
-            // prefetch the next brick's window into the other buffer (free: the
-            // barrier at the end of the previous iteration retired its readers)
-            const int next = atomicAdd(&a.sb.counters[CTR_WORK_G2P], 1);
-            s_item[buf ^ 1] = next;
-            if (next < n_act) issue_halo(a, next, vw[buf ^ 1], &bar[buf ^ 1]);
-        }
-        const bool ok = mbar_wait_bounded(&bar[buf], phase[buf]);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) atomicOr(&a.err[a.sb.act_scene[item]], MPM_EBIT_TIMEOUT);
-            mbar_wait_bounded(&bar[buf], phase[buf]);  // let copies in flight land before leaving
-            mbar_wait_bounded(&bar[buf ^ 1], phase[buf ^ 1]);
-            return;
-        }
-        phase[buf] ^= 1u;
-        const int b = a.sb.act_brick[item], start = a.sb.act_start[item], count = a.sb.act_count[item];
-        const int scene = a.sb.act_scene[item];
+        if (!walker_next(a, n_act, vw, bar, s_item, work, buf, phase, item)) return;
+        const int start = a.sb.act_start[item], count = a.sb.act_count[item], scene = a.sb.act_scene[item];
         const SceneDev sc = a.scenes[scene];
-        const int n = sc.n, nb = sc.nb, lb = b - sc.brick_base;
+        const int nb = sc.nb, lb = a.sb.act_brick[item] - sc.brick_base;
         const int ox = (lb / (nb * nb)) * 4, oy = ((lb / nb) % nb) * 4, oz = (lb % nb) * 4;
-        const float fn = (float)n, dt = a.dt;
-        const float4* win = vw[buf];
         unsigned ebits = 0;
         for (int k0 = 0; k0 < count; k0 += BLOCK) {
             const int k = k0 + tid;
             const bool valid = k < count;
             int key = 0;
             if (valid) {
-                const int p = a.sb.perm[start + k];
-                const int s = start + k;
-                const float x0 = a.in.x[p], x1 = a.in.x[cap + p], x2 = a.in.x[2 * cap + p];
-                int b0, b1, b2;
-                base_cell(x0, n, b0);
-                base_cell(x1, n, b1);
-                base_cell(x2, n, b2);
-                const float f0 = __fmaf_rn(x0, fn, -(float)b0);
-                const float f1 = __fmaf_rn(x1, fn, -(float)b1);
-                const float f2 = __fmaf_rn(x2, fn, -(float)b2);
-                float w0[3], w1[3], w2[3];
-                bspline(f0, w0);
-                bspline(f1, w1);
-                bspline(f2, w2);
-                const int l0 = min(max(b0 - ox, 0), 3), l1 = min(max(b1 - oy, 0), 3), l2 = min(max(b2 - oz, 0), 3);
-                float v0 = 0.f, v1 = 0.f, v2 = 0.f;
-                float B[9];
-#pragma unroll
-                for (int i = 0; i < 9; ++i) B[i] = 0.f;
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    const int wi = l0 + i;
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) {
-                        const int wj = l1 + j;
-                        const float wij = w0[i] * w1[j];
-#pragma unroll
-                        for (int k2 = 0; k2 < 3; ++k2) {
-                            const int wk = l2 + k2;
-                            const int sub = ((wi >> 2) << 2) | ((wj >> 2) << 1) | (wk >> 2);
-                            const float4 g = win[sub * 64 + (wi & 3) * 16 + (wj & 3) * 4 + (wk & 3)];
-                            const float W = wij * w2[k2];
-                            const float g0 = W * g.x, g1 = W * g.y, g2 = W * g.z;
-                            v0 += g0; v1 += g1; v2 += g2;
-                            const float d0 = (float)i - f0, d1 = (float)j - f1, d2 = (float)k2 - f2;
-                            B[0] += g0 * d0; B[1] += g0 * d1; B[2] += g0 * d2;
-                            B[3] += g1 * d0; B[4] += g1 * d1; B[5] += g1 * d2;
-                            B[6] += g2 * d0; B[7] += g2 * d1; B[8] += g2 * d2;
-                        }
-                    }
-                }
-                // C = D^-1 sum N v (x_I - x_p)^T = 4/dx^2 * dx * B  (Eq. 9); x += dt v (Eq. 4)
-                const float c4 = 4.0f * fn;
-#pragma unroll
-                for (int i = 0; i < 9; ++i) B[i] *= c4;
-                const float xn0 = x0 + dt * v0, xn1 = x1 + dt * v1, xn2 = x2 + dt * v2;
-                a.out.x[s] = xn0; a.out.x[cap + s] = xn1; a.out.x[2 * cap + s] = xn2;
-                a.out.v[s] = v0; a.out.v[cap + s] = v1; a.out.v[2 * cap + s] = v2;
-#pragma unroll
-                for (int i = 0; i < 9; ++i) a.out.C[(size_t)i * cap + s] = B[i];
-                a.out.id[s] = a.in.id[p];
-                float mu, lam;
-                if (sc.pp_mat) {
-                    mu = a.in.mu[p];
-                    lam = a.in.lam[p];
-                    a.out.mu[s] = mu;
-                    a.out.lam[s] = lam;
-                } else {
-                    mu = sc.mu;
-                    lam = sc.lam;
-                }
+                G2POut o;
+                ebits |= g2p_particle(a, sc, vw[buf], a.sb.perm[start + k], start + k, ox, oy, oz, o);
                 unsigned ood = 0;
-                key = brick_key(sc, xn0, xn1, xn2, ood);
-                // F <- (I + dt C) F  (Eq. 10)
-                float Fn[9];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const float F0 = a.in.F[(size_t)c * cap + p], F1 = a.in.F[(size_t)(3 + c) * cap + p],
-                                F2 = a.in.F[(size_t)(6 + c) * cap + p];
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) {
-                        const float Fr = r == 0 ? F0 : (r == 1 ? F1 : F2);
-                        Fn[3 * r + c] = Fr + dt * (B[3 * r] * F0 + B[3 * r + 1] * F1 + B[3 * r + 2] * F2);
-                    }
-                }
-                // plasticity and stress: the last step of the G2P loop (Algorithm 1)
-                float t6[6];
-                ebits |= constitutive(a.model, a.plasticity, a.yield_stress, mu, lam, Fn, t6);
-#pragma unroll
-                for (int i = 0; i < 9; ++i) a.out.F[(size_t)i * cap + s] = Fn[i];
-#pragma unroll
-                for (int i = 0; i < 6; ++i) a.out.tau[(size_t)i * cap + s] = t6[i];
-                float chk = xn0 + xn1 + xn2 + v0 + v1 + v2;
-#pragma unroll
-                for (int i = 0; i < 9; ++i) chk += Fn[i];
-                if (!isfinite(chk)) ebits |= MPM_EBIT_NONFINITE;
-                else if (ood) ebits |= MPM_EBIT_OUT_OF_DOMAIN;
+                key = brick_key(sc, o.x[0], o.x[1], o.x[2], ood);
+                if (ood && !(ebits & MPM_EBIT_NONFINITE)) ebits |= MPM_EBIT_OUT_OF_DOMAIN;
             }
             const int rank = aggregated_rank(a.sb.cnt, key, valid);
             if (valid) {
                 a.sb.key[start + k] = key;
                 a.sb.rank[start + k] = rank;
             }
+        }
+        if (ebits) atomicOr(&a.err[scene], ebits);
+        __syncthreads();
+        buf ^= 1;
+    }
+}
+
+// ------------------------------------------------------- fused G2P + P2G
+//
+// G2P of substep k fused with P2G of substep k+1: each particle is read and
+// written once per substep, and its new stress goes from registers straight
+// into the next P2G.  The CTA of a brick scatters into an 8^3-node window
+// around the brick (base cells may have moved by up to one cell): particles
+// whose new base cell is still inside the brick use the per-cell register
+// accumulation of k_p2g; the few that crossed a brick face use shared atomics
+// into the window; any that moved farther use global atomics.
+
+constexpr int kFusedThreads = 192;  // 64 cells x 3 slices
+constexpr int kW8 = 8, kW8Nodes = kW8 * kW8 * kW8;
+
+__global__ void __launch_bounds__(kFusedThreads, 4) k_g2p2g(StepArgs a)
+{
+    __shared__ __align__(128) float4 vw[2][8 * 64];
+    __shared__ float rec[kRecFields][kFusedThreads];
+    __shared__ float win[4][kW8Nodes];
+    __shared__ short order[kFusedThreads];
+    __shared__ int cell_cnt[64], cell_off[65];
+    __shared__ __align__(8) unsigned long long bar[2];
+    __shared__ int s_item[2];
+    const int tid = threadIdx.x;
+    const int cell = tid & 63, slice = tid >> 6;
+    const int cx = cell >> 4, cy = (cell >> 2) & 3, cz = cell & 3;
+    const int n_act = a.sb.counters[CTR_N_ACT];
+    int* work = &a.sb.counters[CTR_WORK_G2P];
+    walker_init<kFusedThreads>(a, n_act, vw, bar, s_item, work);
+    unsigned phase[2] = {0u, 0u};
+    int buf = 0;
+    for (;;) {
+        const int item = s_item[buf];
+        if (item >= n_act) break;
+        for (int t = tid; t < 4 * kW8Nodes; t += kFusedThreads) (&win[0][0])[t] = 0.0f;
+        if (tid < 64) cell_cnt[tid] = 0;
+        if (!walker_next(a, n_act, vw, bar, s_item, work, buf, phase, item)) return;
+        const int start = a.sb.act_start[item], count = a.sb.act_count[item], scene = a.sb.act_scene[item];
+        const SceneDev sc = a.scenes[scene];
+        const int n = sc.n, nb = sc.nb, lb = a.sb.act_brick[item] - sc.brick_base;
+        const int ox = (lb / (nb * nb)) * 4, oy = ((lb / nb) % nb) * 4, oz = (lb % nb) * 4;
+        const float fn = (float)n, dxs = 1.0f / fn;
+        const float m = sc.m_p;
+        const float kA = a.dt * sc.V0 * 4.0f * fn * fn;
+        unsigned ebits = 0;
+        for (int k0 = 0; k0 < count; k0 += kFusedThreads) {
+            const int k = k0 + tid;
+            const bool valid = k < count;
+            int key = 0, my_cell = -1, my_rank = 0;
+            if (valid) {
+                G2POut o;
+                ebits |= g2p_particle(a, sc, vw[buf], a.sb.perm[start + k], start + k, ox, oy, oz, o);
+                // P2G of the next substep at the new position
+                int bc[3];
+                float f[3], w[9];
+                const unsigned ood = particle_weights(o.x[0], o.x[1], o.x[2], n, bc, f, w);
+                if (ood && !(ebits & MPM_EBIT_NONFINITE)) ebits |= ood;
+                key = sc.brick_base + ((bc[0] >> 2) * nb + (bc[1] >> 2)) * nb + (bc[2] >> 2);
+                float q3[3], Ad[9];
+                p2g_coeffs(m, kA, dxs, o.v, o.C, o.t6, f, q3, Ad);
+                const int l0 = bc[0] - ox, l1 = bc[1] - oy, l2 = bc[2] - oz;
+                if ((unsigned)l0 < 4u && (unsigned)l1 < 4u && (unsigned)l2 < 4u) {
+                    put_record<kFusedThreads>(rec, tid, w, q3, Ad);
+                    my_cell = (l0 * 4 + l1) * 4 + l2;
+                    my_rank = atomicAdd(&cell_cnt[my_cell], 1);
+                } else if (l0 >= -1 && l0 <= 4 && l1 >= -1 && l1 <= 4 && l2 >= -1 && l2 <= 4) {
+                    // crossed a brick face: scatter into the window with shared atomics
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+#pragma unroll
+                        for (int j = 0; j < 3; ++j)
+#pragma unroll
+                            for (int k2 = 0; k2 < 3; ++k2) {
+                                const float W = w[i] * w[3 + j] * w[6 + k2];
+                                const int node = ((l0 + 1 + i) * kW8 + (l1 + 1 + j)) * kW8 + (l2 + 1 + k2);
+                                atomicAdd(&win[0][node], W * m);
+                                atomicAdd(&win[1][node], W * (q3[0] + Ad[0] * i + Ad[1] * j + Ad[2] * k2));
+                                atomicAdd(&win[2][node], W * (q3[1] + Ad[3] * i + Ad[4] * j + Ad[5] * k2));
+                                atomicAdd(&win[3][node], W * (q3[2] + Ad[6] * i + Ad[7] * j + Ad[8] * k2));
+                            }
+                } else {
+                    // moved more than a cell: straight to HBM
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+#pragma unroll
+                        for (int j = 0; j < 3; ++j)
+#pragma unroll
+                            for (int k2 = 0; k2 < 3; ++k2) {
+                                const float W = w[i] * w[3 + j] * w[6 + k2];
+                                red_add_v4(&a.G[node_index(sc, bc[0] + i, bc[1] + j, bc[2] + k2)], W * m,
+                                           W * (q3[0] + Ad[0] * i + Ad[1] * j + Ad[2] * k2),
+                                           W * (q3[1] + Ad[3] * i + Ad[4] * j + Ad[5] * k2),
+                                           W * (q3[2] + Ad[6] * i + Ad[7] * j + Ad[8] * k2));
+                            }
+                }
+            }
+            const int rank = aggregated_rank(a.sb.cnt, key, valid);
+            if (valid) {
+                a.sb.key[start + k] = key;
+                a.sb.rank[start + k] = rank;
+            }
+            __syncthreads();
+            scan_cells(cell_cnt, cell_off, tid);
+            __syncthreads();
+            if (my_cell >= 0) order[cell_off[my_cell] + my_rank] = (short)tid;
+            __syncthreads();
+            float acc_w[9], acc_p[9][3];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) { acc_w[q] = 0.f; acc_p[q][0] = acc_p[q][1] = acc_p[q][2] = 0.f; }
+            cell_accumulate<kFusedThreads>(rec, order, cell_off[cell], cell_off[cell + 1], slice, acc_w, acc_p);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                if (acc_w[q] != 0.f) {
+                    const int node = ((cx + 1 + slice) * kW8 + (cy + 1 + q / 3)) * kW8 + (cz + 1 + q % 3);
+                    atomicAdd(&win[0][node], acc_w[q] * m);
+                    atomicAdd(&win[1][node], acc_p[q][0]);
+                    atomicAdd(&win[2][node], acc_p[q][1]);
+                    atomicAdd(&win[3][node], acc_p[q][2]);
+                }
+            }
+            __syncthreads();
+            if (tid < 64) cell_cnt[tid] = 0;
+            __syncthreads();
+        }
+        // window -> HBM (node (ox-1, oy-1, oz-1) + (wi, wj, wk))
+        for (int t = tid; t < kW8Nodes; t += kFusedThreads) {
+            const float mm = win[0][t];
+            if (mm == 0.0f) continue;
+            const int gi = ox - 1 + t / (kW8 * kW8), gj = oy - 1 + (t / kW8) % kW8, gk = oz - 1 + t % kW8;
+            if (gi < 0 || gj < 0 || gk < 0 || gi >= n || gj >= n || gk >= n) continue;
+            red_add_v4(&a.G[node_index(sc, gi, gj, gk)], mm, win[1][t], win[2][t], win[3][t]);
         }
         if (ebits) atomicOr(&a.err[scene], ebits);
         __syncthreads();
@@ -1079,6 +1297,19 @@ cudaError_t launch_g2p(const StepArgs& a, cudaStream_t s)
     default: k_g2p<256><<<a.persistent_ctas, 256, 0, s>>>(a); break;
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_g2p2g(const StepArgs& a, cudaStream_t s)
+{
+    k_g2p2g<<<a.fused_ctas, kFusedThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+int occupancy_g2p2g()
+{
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p2g, kFusedThreads, 0);
+    return b;
 }
 
 cudaError_t launch_gather_field(const PState& st, int cap, int p0, int np, int field, void* dst, cudaStream_t s)

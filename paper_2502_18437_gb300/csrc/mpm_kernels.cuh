@@ -50,10 +50,11 @@ struct StepArgs {
     float yield_stress;
     int persistent_ctas;         // CTAs of the persistent G2P kernel
     int p2g_ctas, grid_ctas;     // CTAs of the persistent P2G and grid kernels
+    int fused_ctas;              // CTAs of the fused G2P + P2G kernel
     int p2g_chunk, g2p_threads;
 };
 
-constexpr int kStateFloats = 32;  // x3 v3 C9 F9 tau6 mu lam (+ int id)
+constexpr int kStateFloats = 26;  // x3 v3 C9 F9 mu lam (+ int id)
 constexpr int kP2GThreads = 192;  // 64 cells x 3 node slices
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
@@ -64,6 +65,8 @@ cudaError_t launch_sort(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_p2g(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_grid(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_g2p(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_g2p2g(const StepArgs& a, cudaStream_t s);
+int occupancy_g2p2g();
 
 // state I/O helpers
 cudaError_t launch_gather_field(const PState& st, int cap, int p0, int np, int field, void* dst,

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libmpm_gb300.so")
 MPM_OK = 0
 STATUS = {
     -1: "INVALID_ARGUMENT", -2: "OUT_OF_MEMORY", -3: "CUDA", -4: "OUT_OF_DOMAIN", -5: "NONFINITE",
-    -6: "INVERTED", -7: "CAPACITY", -8: "TIMEOUT", -9: "STATE",
+    -6: "INVERTED", -7: "CAPACITY", -8: "TIMEOUT", -9: "STATE", -10: "INTERNAL",
 }
 MEM_HOST, MEM_DEVICE = 0, 1
 MODELS = {"fixed_corotated": 0, "neo_hookean": 1}
@@ -28,10 +28,10 @@ RIGID_TYPES = {"sphere": 0, "box": 1, "quad_slicer": 2, "segments": 3, "none": -
 FIELD = {"x": 1, "v": 2, "C": 4, "F": 8, "order": 16, "impulse": 32}
 FIELD_SHAPE = {"x": (3,), "v": (3,), "C": (3, 3), "F": (3, 3), "order": ()}
 OPT = {"use_graphs": 1, "launch_mode": 2, "p2g_threads": 3, "g2p_threads": 4, "ctas_per_sm": 5, "graph_chunk": 6,
-       "phase_timing": 7, "p2g_chunk": 8}
+       "phase_timing": 7, "p2g_chunk": 8, "fused": 9}
 MAX_PTS = 64
 MAX_RIGIDS = 8
-EBIT = {"out_of_domain": 1, "nonfinite": 2, "inverted": 4, "timeout": 8}
+EBIT = {"out_of_domain": 1, "nonfinite": 2, "inverted": 4, "timeout": 8, "internal": 16}
 
 
 class MPMError(RuntimeError):

@@ -148,7 +148,8 @@ def test_sort_by_brick_order():
 def test_graph_direct_and_looped_agree():
     sc = W.tissue_slab(cells=(32, 6, 32), lo=(0.3, 0.2, 0.3), size=(0.4, 0.08, 0.4), n=32, substeps=20)
     outs = []
-    for opts in ({"use_graphs": 1}, {"use_graphs": 0}, {"launch_mode": 1}):
+    for opts in ({"use_graphs": 1}, {"use_graphs": 0}, {"launch_mode": 1}, {"fused": 0},
+                 {"fused": 0, "p2g_chunk": 192}):
         with mpm.from_workload(sc) as sim:
             for k, v in opts.items():
                 sim.set_option(k, v)
