@@ -56,9 +56,10 @@ PState state_view(float* base, int cap)
     s.v = base + 3 * (size_t)cap;
     s.C = base + 6 * (size_t)cap;
     s.F = base + 15 * (size_t)cap;
-    s.mu = base + 24 * (size_t)cap;
-    s.lam = base + 25 * (size_t)cap;
-    s.id = reinterpret_cast<int*>(base + 26 * (size_t)cap);
+    s.tau = base + 24 * (size_t)cap;
+    s.mu = base + 30 * (size_t)cap;
+    s.lam = base + 31 * (size_t)cap;
+    s.id = reinterpret_cast<int*>(base + 32 * (size_t)cap);
     return s;
 }
 
@@ -172,6 +173,7 @@ int enqueue_substep(mpm_ctx* c, float dt, const PState& in, const PState& out, b
         const int s0 = c->launch_mode == 1 ? g : 0;
         const int s1 = c->launch_mode == 1 ? g + 1 : c->n_scenes;
         StepArgs a = step_args(c, dt, s0, s1, in, out);
+        a.tau_valid = c->tau_valid;
         cudaEvent_t* ev = nullptr;
         if (c->phase_timing) {
             if (c->phase_used + 5 > c->phase_events.size()) {
@@ -195,6 +197,8 @@ int enqueue_substep(mpm_ctx* c, float dt, const PState& in, const PState& out, b
         else MPM_CK(launch_g2p(a, c->stream));
         if (ev) MPM_CK(cudaEventRecord(ev[4], c->stream));
     }
+    // the unfused G2P stores the new stress; the fused kernel keeps it in registers
+    c->tau_valid = !c->fused;
     return MPM_OK;
 }
 
@@ -202,6 +206,7 @@ int enqueue_substep(mpm_ctx* c, float dt, const PState& in, const PState& out, b
 int invalidate_pending(mpm_ctx* c)
 {
     c->g_pending = false;
+    c->tau_valid = false;
     return MPM_OK;
 }
 

@@ -51,6 +51,7 @@ struct mpm_ctx {
     bool g_pending = false;
     bool g_dirty = false;  // G may hold a pending scatter (must be cleared before a fresh P2G)
     float g_dt = 0.f;
+    bool tau_valid = false;  // the stored stress matches the stored F
 
     // options
     int use_graphs = 1;

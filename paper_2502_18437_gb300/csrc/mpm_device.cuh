@@ -3,7 +3,7 @@
 //
 // Layout in HBM
 //  - particles: structure of arrays, component-major: x[3][cap], v[3][cap],
-//    C[9][cap], F[9][cap], mu[cap], lam[cap], id[cap].  Two copies ping-pong:
+//    C[9][cap], F[9][cap], tau[6][cap], mu[cap], lam[cap], id[cap].  Two copies ping-pong:
 //    each substep reads one through the sort permutation and G2P writes the
 //    other in sorted order, so particles stay sorted by brick in storage.
 //  - grid: each scene owns a dense block of (n/4)^3 bricks of 4^3 nodes;
@@ -64,6 +64,7 @@ struct PState {
     float* v;
     float* C;
     float* F;
+    float* tau;  // Kirchhoff stress of F (xx xy xz yy yz zz), written by the unfused G2P
     float* mu;
     float* lam;
     int* id;

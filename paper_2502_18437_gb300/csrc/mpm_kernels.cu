@@ -511,15 +511,22 @@ __global__ void __launch_bounds__(kP2GThreads, CHUNK == kP2GThreads ? 5 : 4) k_p
                     int bc[3];
                     float f[3], w[9];
                     ebits |= particle_weights(a.in.x[p], a.in.x[cap + p], a.in.x[2 * cap + p], n, bc, f, w);
-                    float F[9], C[9], v[3], t6[6];
-#pragma unroll
-                    for (int q = 0; q < 9; ++q) F[q] = a.in.F[(size_t)q * cap + p];
+                    float C[9], v[3], t6[6];
 #pragma unroll
                     for (int q = 0; q < 9; ++q) C[q] = a.in.C[(size_t)q * cap + p];
 #pragma unroll
                     for (int q = 0; q < 3; ++q) v[q] = a.in.v[(size_t)q * cap + p];
-                    const float mu = sc.pp_mat ? a.in.mu[p] : sc.mu, lam = sc.pp_mat ? a.in.lam[p] : sc.lam;
-                    ebits |= constitutive(a.model, 0, 0.f, mu, lam, F, t6);  // stress of the current F
+                    if (a.tau_valid) {
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) t6[q] = a.in.tau[(size_t)q * cap + p];
+                    } else {
+                        // stress of the current F (after host writes, or seeding a fused run)
+                        float F[9];
+#pragma unroll
+                        for (int q = 0; q < 9; ++q) F[q] = a.in.F[(size_t)q * cap + p];
+                        const float mu = sc.pp_mat ? a.in.mu[p] : sc.mu, lam = sc.pp_mat ? a.in.lam[p] : sc.lam;
+                        ebits |= constitutive(a.model, 0, 0.f, mu, lam, F, t6);
+                    }
                     float q3[3], Ad[9];
                     p2g_coeffs(m, kA, dxs, v, C, t6, f, q3, Ad);
                     put_record<CHUNK>(rec, k, w, q3, Ad);
@@ -1037,6 +1044,8 @@ __global__ void __launch_bounds__(BLOCK, 768 / BLOCK) k_g2p(StepArgs a)
             if (valid) {
                 G2POut o;
                 ebits |= g2p_particle(a, sc, vw[buf], a.sb.perm[start + k], start + k, ox, oy, oz, o);
+#pragma unroll
+                for (int q = 0; q < 6; ++q) a.out.tau[(size_t)q * a.cap + start + k] = o.t6[q];
                 unsigned ood = 0;
                 key = brick_key(sc, o.x[0], o.x[1], o.x[2], ood);
                 if (ood && !(ebits & MPM_EBIT_NONFINITE)) ebits |= MPM_EBIT_OUT_OF_DOMAIN;

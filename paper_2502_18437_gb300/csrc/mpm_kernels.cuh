@@ -52,9 +52,10 @@ struct StepArgs {
     int p2g_ctas, grid_ctas;     // CTAs of the persistent P2G and grid kernels
     int fused_ctas;              // CTAs of the fused G2P + P2G kernel
     int p2g_chunk, g2p_threads;
+    int tau_valid;               // P2G reads the stored stress (else recomputes it from F)
 };
 
-constexpr int kStateFloats = 26;  // x3 v3 C9 F9 mu lam (+ int id)
+constexpr int kStateFloats = 32;  // x3 v3 C9 F9 tau6 mu lam (+ int id)
 constexpr int kP2GThreads = 192;  // 64 cells x 3 node slices
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
