@@ -11,85 +11,9 @@
 //              staged by bulk-copy TMA, plasticity, next brick key + rank
 #include <cstdio>
 
-#include "mpm_kernels.cuh"
+#include "mpm_transfer.cuh"
 
 namespace mpm {
-
-// ------------------------------------------------------------ PTX helpers
-
-__device__ __forceinline__ unsigned smem_u32(const void* p)
-{
-    return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
-{
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release(unsigned* p, unsigned v)
-{
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ void red_add_v4(float4* addr, float a, float b, float c, float d)
-{
-    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init()
-{
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait on an mbarrier phase; false when the bound ran out.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity)
-{
-    for (int it = 0; it < (1 << 22); ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
-constexpr unsigned kFull = 0xffffffffu;
 
 // ----------------------------------------------------------------- scan
 //
@@ -277,11 +201,12 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(StepArgs a)
 }
 
 // Counting-sort scatter; also clears the scan's tile state for the next substep.
-__global__ void k_scatter(StepArgs a, int n_tiles)
+// write_perm = 0 only clears (the adjoint reuses a recorded permutation).
+__global__ void k_scatter(StepArgs a, int n_tiles, int write_perm)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = a.r.p0 + g;
-    if (g < a.r.np) {
+    if (write_perm && g < a.r.np) {
         const int key = a.sb.key[i];
         const int dst = (key >= a.r.bb0 && key < a.r.bb0 + a.r.nbr) ? __ldg(&a.sb.off[key]) + a.sb.rank[i] : -1;
         if (dst >= a.r.p0 && dst < a.r.p0 + a.r.np) a.sb.perm[dst] = i;
@@ -289,33 +214,6 @@ __global__ void k_scatter(StepArgs a, int n_tiles)
     }
     if (g < n_tiles) a.sb.tile_status[g] = 0u;
     if (g == 0) a.sb.counters[CTR_TICKET] = 0;
-}
-
-// ----------------------------------------------------- brick key + rank
-
-__device__ __forceinline__ int brick_key(const SceneDev& sc, float x0, float x1, float x2, unsigned& ood)
-{
-    int c0, c1, c2;
-    ood |= (unsigned)(base_cell(x0, sc.n, c0) | base_cell(x1, sc.n, c1) | base_cell(x2, sc.n, c2));
-    return sc.brick_base + ((c0 >> 2) * sc.nb + (c1 >> 2)) * sc.nb + (c2 >> 2);
-}
-
-// Warp-aggregated rank: lanes with the same key get consecutive ranks from one
-// atomic.  Must be called by all 32 lanes; `valid` marks lanes with a particle.
-__device__ __forceinline__ int aggregated_rank(int* cnt, int key, bool valid)
-{
-    const unsigned active = __ballot_sync(kFull, valid);
-    int rank = 0;
-    const unsigned peers = __match_any_sync(kFull, valid ? key : -1) & active;
-    if (valid) {
-        const int lane = threadIdx.x & 31;
-        const int leader = __ffs(peers) - 1;
-        int base = 0;
-        if (lane == leader) base = atomicAdd(&cnt[key], __popc(peers));
-        base = __shfl_sync(peers, base, leader);
-        rank = base + __popc(peers & ((1u << lane) - 1u));
-    }
-    return rank;
 }
 
 // Keys and ranks of the stored particles after the host changed positions
@@ -346,109 +244,6 @@ __global__ void k_prepare(StepArgs a, PState st)
         a.sb.rank[i] = rank;
         if (ebits) atomicOr(&a.err[scene], ebits);
     }
-}
-
-// ------------------------------------------------------ transfer helpers
-
-constexpr int kRecFields = 21;  // w0[3] w1[3] w2[3] q[3] Ad[9]
-
-// Base cells, fractional offsets and quadratic B-spline weights of a position.
-__device__ __forceinline__ unsigned particle_weights(float x0, float x1, float x2, int n, int b[3], float f[3],
-                                                     float w[9])
-{
-    const float fn = (float)n;
-    const unsigned ood = base_cell(x0, n, b[0]) | base_cell(x1, n, b[1]) | base_cell(x2, n, b[2]);
-    f[0] = __fmaf_rn(x0, fn, -(float)b[0]);
-    f[1] = __fmaf_rn(x1, fn, -(float)b[1]);
-    f[2] = __fmaf_rn(x2, fn, -(float)b[2]);
-    bspline(f[0], w);
-    bspline(f[1], w + 3);
-    bspline(f[2], w + 6);
-    return ood ? MPM_EBIT_OUT_OF_DOMAIN : 0u;
-}
-
-// P2G coefficients (Eq. 8 with the APIC particle momentum, M^-1 = 4/dx^2 of
-// Eq. 7, V sigma = V0 tau): the momentum a particle gives node (i,j,k) of its
-// stencil is W_ijk (q + Ad (i,j,k)) with Ad = (m C - dt V0 M^-1 tau) dx and
-// q = m v - Ad f, so that Ad ((i,j,k) - f) = A (x_I - x_p).
-__device__ __forceinline__ void p2g_coeffs(float m, float kA, float dxs, const float v[3], const float C[9],
-                                           const float t6[6], const float f[3], float q[3], float Ad[9])
-{
-    const float tau[9] = {t6[0], t6[1], t6[2], t6[1], t6[3], t6[4], t6[2], t6[4], t6[5]};
-#pragma unroll
-    for (int i = 0; i < 9; ++i) Ad[i] = (m * C[i] - kA * tau[i]) * dxs;
-#pragma unroll
-    for (int r = 0; r < 3; ++r) q[r] = m * v[r] - (Ad[3 * r] * f[0] + Ad[3 * r + 1] * f[1] + Ad[3 * r + 2] * f[2]);
-}
-
-template <int N>
-__device__ __forceinline__ void put_record(float (*rec)[N], int k, const float w[9], const float q[3], const float Ad[9])
-{
-#pragma unroll
-    for (int i = 0; i < 9; ++i) rec[i][k] = w[i];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) rec[9 + i][k] = q[i];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) rec[12 + i][k] = Ad[i];
-}
-
-// Phase B of the per-cell accumulation: thread (cell, slice) adds the
-// contributions of the particles of its cell (order[beg..end)) to the 9 nodes
-// cell + (slice, j, k) in registers.
-template <int N>
-__device__ __forceinline__ void cell_accumulate(const float (*rec)[N], const short* order, int beg, int end, int slice,
-                                                float acc_w[9], float acc_p[9][3])
-{
-    const float si = (float)slice;
-    for (int j = beg; j < end; ++j) {
-        const int k = order[j];
-        const float wi = rec[slice][k];
-        const float wy[3] = {rec[3][k], rec[4][k], rec[5][k]};
-        const float wz[3] = {rec[6][k], rec[7][k], rec[8][k]};
-        // r(j,k) = q + Ad (slice, j, k)
-        const float r0 = rec[9][k] + si * rec[12][k], r1 = rec[10][k] + si * rec[15][k], r2 = rec[11][k] + si * rec[18][k];
-        const float a01 = rec[13][k], a11 = rec[16][k], a21 = rec[19][k];
-        const float a02 = rec[14][k], a12 = rec[17][k], a22 = rec[20][k];
-#pragma unroll
-        for (int jj = 0; jj < 3; ++jj) {
-            const float wij = wi * wy[jj];
-            const float s0 = r0 + a01 * jj, s1 = r1 + a11 * jj, s2 = r2 + a21 * jj;
-#pragma unroll
-            for (int kk = 0; kk < 3; ++kk) {
-                const float W = wij * wz[kk];
-                const int q = jj * 3 + kk;
-                acc_w[q] += W;
-                acc_p[q][0] += W * (s0 + a02 * kk);
-                acc_p[q][1] += W * (s1 + a12 * kk);
-                acc_p[q][2] += W * (s2 + a22 * kk);
-            }
-        }
-    }
-}
-
-// Exclusive scan of the 64 per-cell counts by warp 0.
-__device__ __forceinline__ void scan_cells(const int* cell_cnt, int* cell_off, int tid)
-{
-    if (tid < 32) {
-        const int c_a = cell_cnt[2 * tid], c_b = cell_cnt[2 * tid + 1];
-        int incl = c_a + c_b;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int t = __shfl_up_sync(kFull, incl, d);
-            if (tid >= d) incl += t;
-        }
-        const int excl = incl - c_a - c_b;
-        cell_off[2 * tid] = excl;
-        cell_off[2 * tid + 1] = excl + c_a;
-        if (tid == 31) cell_off[64] = incl;
-    }
-}
-
-// Global node index of node (gi, gj, gk) of a scene (brick layout).
-__device__ __forceinline__ int node_index(const SceneDev& sc, int gi, int gj, int gk)
-{
-    const int brick = sc.brick_base + ((gi >> 2) * sc.nb + (gj >> 2)) * sc.nb + (gk >> 2);
-    return brick * 64 + (gi & 3) * 16 + (gj & 3) * 4 + (gk & 3);
 }
 
 // ------------------------------------------------------------------ P2G
@@ -858,26 +653,6 @@ __global__ void __launch_bounds__(kGridThreads) k_grid(StepArgs a)
 // velocity window are staged in shared memory by bulk-copy TMA, double
 // buffered: the next brick's window is in flight while this brick computes.
 
-__device__ __forceinline__ void issue_halo(const StepArgs& a, int item, float4* dst, unsigned long long* bar)
-{
-    const int b = a.sb.act_brick[item];
-    const SceneDev& sc = a.scenes[a.sb.act_scene[item]];
-    const int nb = sc.nb, lb = b - sc.brick_base;
-    const int bx = lb / (nb * nb), by = (lb / nb) % nb, bz = lb % nb;
-    fence_proxy_async();
-    unsigned bytes = 0;
-#pragma unroll
-    for (int o = 0; o < 8; ++o)
-        if (bx + (o >> 2) < nb && by + ((o >> 1) & 1) < nb && bz + (o & 1) < nb) bytes += 64 * sizeof(float4);
-    mbar_expect_tx(bar, bytes);
-#pragma unroll
-    for (int o = 0; o < 8; ++o) {
-        const int ex = bx + (o >> 2), ey = by + ((o >> 1) & 1), ez = bz + (o & 1);
-        if (ex < nb && ey < nb && ez < nb)
-            bulk_g2s(dst + o * 64, &a.V[(sc.brick_base + (ex * nb + ey) * nb + ez) * 64], 64 * sizeof(float4), bar);
-    }
-}
-
 // G2P of one particle from the staged window (Eq. 4, Eq. 9, Eq. 10) followed by
 // the constitutive update (the last step of the G2P loop in Algorithm 1).
 // Writes x, v, C, F (and id, mu, lam) to slot s of the output state; returns
@@ -969,51 +744,6 @@ __device__ __forceinline__ unsigned g2p_particle(const StepArgs& a, const SceneD
     for (int i = 0; i < 9; ++i) chk += Fn[i];
     if (!isfinite(chk)) ebits |= MPM_EBIT_NONFINITE;
     return ebits;
-}
-
-// Shared prologue of the brick-walking kernels: mbarriers, first halo, clocks.
-template <int BLOCK>
-__device__ __forceinline__ void walker_init(const StepArgs& a, int n_act, float4 (*vw)[8 * 64], unsigned long long* bar,
-                                            int* s_item, int* work)
-{
-    const int tid = threadIdx.x;
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        fence_mbar_init();
-        const int first = atomicAdd(work, 1);
-        s_item[0] = first;
-        if (first < n_act) issue_halo(a, first, vw[0], &bar[0]);
-    }
-    if (blockIdx.x == 0) {
-        // scene clocks advance once per substep (read by the next grid update)
-        for (int s = a.r.s0 + tid; s < a.r.s1; s += BLOCK) {
-            a.t_scene[s] += (double)a.dt;
-            a.epoch[s] += 1;
-        }
-    }
-    __syncthreads();
-}
-
-// Prefetch the next brick's halo and wait for this one; false on timeout (the
-// CTA must then return).
-__device__ __forceinline__ bool walker_next(const StepArgs& a, int n_act, float4 (*vw)[8 * 64], unsigned long long* bar,
-                                            int* s_item, int* work, int buf, unsigned* phase, int item)
-{
-    if (threadIdx.x == 0) {
-        const int next = atomicAdd(work, 1);
-        s_item[buf ^ 1] = next;
-        if (next < n_act) issue_halo(a, next, vw[buf ^ 1], &bar[buf ^ 1]);
-    }
-    const bool ok = mbar_wait_bounded(&bar[buf], phase[buf]);
-    if (__syncthreads_or(!ok)) {
-        if (threadIdx.x == 0) atomicOr(&a.err[a.sb.act_scene[item]], MPM_EBIT_TIMEOUT);
-        mbar_wait_bounded(&bar[buf], phase[buf]);  // let copies in flight land before leaving
-        mbar_wait_bounded(&bar[buf ^ 1], phase[buf ^ 1]);
-        return false;
-    }
-    phase[buf] ^= 1u;
-    return true;
 }
 
 template <int BLOCK>
@@ -1274,14 +1004,14 @@ cudaError_t launch_prepare(const StepArgs& a, const PState& st, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_sort(const StepArgs& a, cudaStream_t s)
+cudaError_t launch_sort(const StepArgs& a, cudaStream_t s, bool write_perm)
 {
     const int n_tiles = (a.r.nbr + kScanTile - 1) / kScanTile;
     k_scan<<<n_tiles, kScanThreads, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int work = a.r.np > n_tiles ? a.r.np : n_tiles;
-    k_scatter<<<n_blocks(work, 256), 256, 0, s>>>(a, n_tiles);
+    k_scatter<<<n_blocks(work, 256), 256, 0, s>>>(a, n_tiles, write_perm ? 1 : 0);
     return cudaGetLastError();
 }
 
