@@ -268,6 +268,35 @@ int mpm_backward(mpm_ctx* ctx, const float* dL_dx, const float* dL_dv, float* dL
  * best time per substep.  Blocks.  Errors: INVALID_ARGUMENT, CUDA, TIMEOUT. */
 int mpm_autotune(mpm_ctx* ctx, float dt, int trial_substeps, float* best_ms_out);
 
+/* ---- allocation-free brick sort --------------------------------------- */
+
+#define MPM_NOALLOC_MAX_PARTICLES 1048576 /* largest N accepted                  */
+#define MPM_NOALLOC_MAX_GRID 256          /* largest n (nodes per dimension)     */
+
+/* The particle sort of mpm_substep (ordering by the 4^3-node brick that holds
+ * each particle's base cell) for callers that must not allocate device memory
+ * while they run: a host loop that cannot take the device-wide synchronisation
+ * of cudaMalloc/cudaFree every frame, work recorded into CUDA graphs (where
+ * allocation is not allowed), or integrations that only lend the library the
+ * buffers they own.  The paper has no counterpart to this call.
+ *
+ * x: device float (N,3) positions of one grid of n^3 nodes (dx = 1/n);
+ * perm: device int[N], receives the particle indices ordered by brick (the
+ * order inside a brick is unspecified); brick_start: device int[(n/4)^3 + 1]
+ * or NULL, receives the first sorted slot of each brick and N at the end.
+ * Work is enqueued on `cuda_stream` (a cudaStream_t; NULL = legacy stream).
+ *
+ * It allocates nothing: its scratch is one static device array of
+ * 10,486,784 bytes that every device loading the library reserves until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make that first
+ * call before any stream capture.  All calls share the array, so calls that
+ * overlap on the GPU race and must be serialised by the caller.
+ * Errors: INVALID_ARGUMENT (n not a multiple of 4 or < 8, N < 0, NULL
+ * buffers), CAPACITY (N > MPM_NOALLOC_MAX_PARTICLES or n > MPM_NOALLOC_MAX_GRID),
+ * CUDA (launch or symbol lookup failed). */
+int mpm_sort_bricks_noalloc(int n, int64_t N, const float* x, int* perm, int* brick_start, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -81,6 +81,7 @@ _SIGS = {
     "mpm_autotune": (ct.c_int, [_P, ct.c_float, ct.c_int, ct.POINTER(ct.c_float)]),
     "mpm_phase_stats": (ct.c_int, [_P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64), ct.POINTER(ct.c_int64),
                                    ct.c_int]),
+    "mpm_sort_bricks_noalloc": (ct.c_int, [ct.c_int, ct.c_int64, _P, _P, _P, _P]),
 }
 
 
@@ -186,6 +187,11 @@ def mpm_phase_stats(h, reset=True):
     act = (ct.c_int64 * 2)()
     _check(lib().mpm_phase_stats(h, ms, ct.byref(n), act, int(reset)), "mpm_phase_stats")
     return {"ms": list(ms), "substeps": n.value, "active_pbricks": act[0], "active_nbricks": act[1]}
+
+
+def mpm_sort_bricks_noalloc(n, N, x_ptr, perm_ptr, brick_start_ptr=None, stream=0):
+    """Allocation-free brick sort (device pointers); returns the status code."""
+    return lib().mpm_sort_bricks_noalloc(int(n), int(N), x_ptr, perm_ptr, brick_start_ptr, _P(stream or 0))
 
 
 # ------------------------------------------------------------- marshalling
