@@ -91,9 +91,12 @@ enum {
     MPM_OPT_GRAPH_CHUNK = 6,    /* substeps captured per graph (1..64)              */
     MPM_OPT_PHASE_TIMING = 7,   /* 0/1: record CUDA events around each phase of every
                                    substep (forces direct launches); see mpm_phase_stats */
-    MPM_OPT_P2G_CHUNK = 8,      /* particles staged per pass of the P2G kernel: 192/384 */
-    MPM_OPT_FUSED = 9           /* 1: fuse each substep's G2P with the next substep's
+    MPM_OPT_P2G_CHUNK = 8,      /* particles staged per pass of the P2G kernel: 192
+                                   (default) / 384                                  */
+    MPM_OPT_FUSED = 9,          /* 1: fuse each substep's G2P with the next substep's
                                    P2G; 0 (default): separate P2G and G2P kernels */
+    MPM_OPT_G2P_REGS64 = 10     /* 1 (default): G2P variant limited to 64 registers
+                                   (more resident warps); 0: up to 80 registers     */
 };
 
 /* ---- configuration --------------------------------------------------- */
@@ -261,9 +264,11 @@ int mpm_backward(mpm_ctx* ctx, const float* dL_dx, const float* dL_dv, float* dL
 
 /* ---- batching -------------------------------------------------------- */
 
-/* Time candidate launch shapes (P2G chunk, threads per CTA of G2P, persistent
- * CTAs per SM) on `trial_substeps` substeps of size dt and keep the fastest;
- * the particle state, keys, clocks and impulses are restored afterwards, so
+/* Time candidate launch shapes (P2G chunk, threads per CTA and register
+ * budget of G2P, persistent CTAs per SM) on `trial_substeps` substeps of size dt and keep the fastest.
+ * Each trial is timed as the user's substeps run: one graph replay of the
+ * substeps (rounded up to an even count) when graphs are on, else direct
+ * launches.  The particle state, keys, clocks and impulses are restored afterwards, so
  * the simulation does not advance.  *best_ms_out (may be NULL) receives the
  * best time per substep.  Blocks.  Errors: INVALID_ARGUMENT, CUDA, TIMEOUT. */
 int mpm_autotune(mpm_ctx* ctx, float dt, int trial_substeps, float* best_ms_out);

@@ -153,10 +153,19 @@ StepArgs step_args(mpm_ctx* c, float dt, int s0, int s1, const PState& in, const
     a.model = c->cfg.model;
     a.plasticity = c->cfg.plasticity;
     a.yield_stress = c->cfg.yield_stress;
-    a.persistent_ctas = c->num_sms * cap_occ(c, occupancy_g2p(c->g2p_threads));
-    a.p2g_ctas = c->num_sms * cap_occ(c, occupancy_p2g(c->p2g_chunk));
-    a.grid_ctas = c->num_sms * 8;
-    a.fused_ctas = c->num_sms * cap_occ(c, occupancy_g2p2g());
+    // the occupancy queries are host calls: ask once per variant and context
+    const int ti = c->g2p_threads == 128 ? 0 : c->g2p_threads == 512 ? 2 : 1;
+    int& og = c->occ_g2p[c->g2p_regs64 ? 1 : 0][ti];
+    if (!og) og = std::max(1, occupancy_g2p(c->g2p_threads, c->g2p_regs64));
+    int& op = c->occ_p2g[c->p2g_chunk == kP2GThreads ? 0 : 1];
+    if (!op) op = std::max(1, occupancy_p2g(c->p2g_chunk));
+    if (!c->occ_grid) c->occ_grid = std::max(1, occupancy_grid());
+    if (!c->occ_fused) c->occ_fused = std::max(1, occupancy_g2p2g());
+    a.persistent_ctas = c->num_sms * cap_occ(c, og);
+    a.g2p_regs64 = c->g2p_regs64;
+    a.p2g_ctas = c->num_sms * cap_occ(c, op);
+    a.grid_ctas = c->num_sms * c->occ_grid;
+    a.fused_ctas = c->num_sms * cap_occ(c, c->occ_fused);
     a.p2g_chunk = c->p2g_chunk;
     a.g2p_threads = c->g2p_threads;
     return a;
@@ -399,6 +408,7 @@ extern "C" int mpm_set_option(mpm_ctx* c, int option, int64_t value)
         c->graph_chunk = (int)value;
         break;
     case MPM_OPT_PHASE_TIMING: c->phase_timing = value != 0; break;
+    case MPM_OPT_G2P_REGS64: c->g2p_regs64 = value != 0; break;
     case MPM_OPT_FUSED:
         c->fused = value != 0;
         invalidate_pending(c);
@@ -809,36 +819,68 @@ extern "C" int mpm_autotune(mpm_ctx* c, float dt, int trial_substeps, float* bes
     cudaError_t ce = copy_all(true);
     if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
     if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
-    int best[3] = {c->p2g_chunk, c->g2p_threads, c->ctas_per_sm};
+    int best[4] = {c->p2g_chunk, c->g2p_threads, c->ctas_per_sm, c->g2p_regs64};
     float best_ms = 3.4e38f;
     const int chunks[2] = {kP2GThreads, 2 * kP2GThreads};
     const int threads[3] = {128, 256, 512};
     const int ctas[2] = {0, 2};
+    const int T = trial_substeps + (trial_substeps & 1);
+    const bool tau_valid0 = c->tau_valid;
+    const bool graphs = c->use_graphs && !c->phase_timing;
     for (int a = 0; a < 2 && ce == cudaSuccess && st == MPM_OK; ++a)
         for (int b = 0; b < 3 && ce == cudaSuccess && st == MPM_OK; ++b)
+            for (int r64 = 0; r64 < 2 && ce == cudaSuccess && st == MPM_OK; ++r64)
             for (int k = 0; k < 2 && ce == cudaSuccess && st == MPM_OK; ++k) {
                 c->p2g_chunk = chunks[a];
                 c->g2p_threads = threads[b];
+                c->g2p_regs64 = r64;
                 c->ctas_per_sm = ctas[k];
-                // one untimed warm-up substep from a clean accumulator, then the timed trial
+                c->tau_valid = tau_valid0;  // the restored state's stored stress
+                // one untimed warm-up substep from a clean accumulator, then the timed trial:
+                // graph replays (an even number of substeps, so that the replayed graph
+                // reads the buffer it was captured for) when graphs are on, else direct launches
                 ce = cudaMemsetAsync(c->G, 0, sizeof(float4) * nbk * 64, c->stream);
                 if (ce == cudaSuccess) st = enqueue_substep(c, dt, c->st[c->cur], c->st[c->cur ^ 1], true);
                 c->cur ^= 1;
-                if (!st && ce == cudaSuccess) ce = cudaEventRecord(e0, c->stream);
-                for (int s = 0; s < trial_substeps && !st && ce == cudaSuccess; ++s) {
-                    st = enqueue_substep(c, dt, c->st[c->cur], c->st[c->cur ^ 1], false);
-                    c->cur ^= 1;
+                if (graphs) {
+                    cudaGraph_t g = nullptr;
+                    cudaGraphExec_t ex = nullptr;
+                    if (!st && ce == cudaSuccess) ce = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+                    if (!st && ce == cudaSuccess) {
+                        int cur = c->cur;
+                        for (int s = 0; s < T && !st; ++s) {
+                            st = enqueue_substep(c, dt, c->st[cur], c->st[cur ^ 1], false);
+                            cur ^= 1;
+                        }
+                        const cudaError_t ce2 = cudaStreamEndCapture(c->stream, &g);
+                        if (ce == cudaSuccess) ce = ce2;
+                    }
+                    if (!st && ce == cudaSuccess) ce = cudaGraphInstantiate(&ex, g, 0);
+                    if (g) cudaGraphDestroy(g);
+                    if (!st && ce == cudaSuccess) ce = cudaGraphLaunch(ex, c->stream);
+                    if (!st && ce == cudaSuccess) ce = cudaEventRecord(e0, c->stream);
+                    if (!st && ce == cudaSuccess) ce = cudaGraphLaunch(ex, c->stream);
+                    if (!st && ce == cudaSuccess) ce = cudaEventRecord(e1, c->stream);
+                    if (!st && ce == cudaSuccess) st = wait_stream(c);
+                    if (ex) cudaGraphExecDestroy(ex);
+                } else {
+                    if (!st && ce == cudaSuccess) ce = cudaEventRecord(e0, c->stream);
+                    for (int s = 0; s < T && !st && ce == cudaSuccess; ++s) {
+                        st = enqueue_substep(c, dt, c->st[c->cur], c->st[c->cur ^ 1], false);
+                        c->cur ^= 1;
+                    }
+                    if (!st && ce == cudaSuccess) ce = cudaEventRecord(e1, c->stream);
+                    if (!st && ce == cudaSuccess) st = wait_stream(c);
                 }
-                if (!st && ce == cudaSuccess) ce = cudaEventRecord(e1, c->stream);
-                if (!st && ce == cudaSuccess) st = wait_stream(c);
                 float ms = 0.f;
                 if (!st && ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
-                ms /= trial_substeps;
+                ms /= T;
                 if (!st && ce == cudaSuccess && ms < best_ms) {
                     best_ms = ms;
                     best[0] = chunks[a];
                     best[1] = threads[b];
                     best[2] = ctas[k];
+                    best[3] = r64;
                 }
                 c->cur = cur0;
                 if (ce == cudaSuccess) ce = copy_all(false);
@@ -848,8 +890,10 @@ extern "C" int mpm_autotune(mpm_ctx* c, float dt, int trial_substeps, float* bes
     // the trials left scatters in G that do not belong to the restored state
     c->g_pending = false;
     c->g_dirty = true;
+    c->tau_valid = tau_valid0;
     c->p2g_chunk = best[0];
     c->g2p_threads = best[1];
+    c->g2p_regs64 = best[3];
     c->ctas_per_sm = best[2];
     clear_graphs(c);
     if (e0) cudaEventDestroy(e0);

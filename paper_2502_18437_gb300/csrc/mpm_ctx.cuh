@@ -56,12 +56,18 @@ struct mpm_ctx {
     // options
     int use_graphs = 1;
     int launch_mode = 0;
-    int p2g_chunk = 2 * mpm::kP2GThreads;
+    int p2g_chunk = mpm::kP2GThreads;
     int g2p_threads = 256;
+    int g2p_regs64 = 1;
     int ctas_per_sm = 0;
     int graph_chunk = 16;
     int phase_timing = 0;
     int fused = 0;
+    // occupancy (resident CTAs per SM) of each kernel variant on this device, 0 = not asked yet
+    int occ_g2p[2][3] = {};
+    int occ_p2g[2] = {};
+    int occ_grid = 0;
+    int occ_fused = 0;
     std::vector<cudaEvent_t> phase_events;  // 5 per timed substep
     size_t phase_used = 0;
     std::map<std::tuple<uint32_t, int, int>, cudaGraphExec_t> graphs;

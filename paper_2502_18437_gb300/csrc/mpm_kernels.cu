@@ -532,6 +532,74 @@ __device__ void flush_impulse(const StepArgs& a, const float* simp, int scene, i
 
 // Grid update of the active node bricks: 64 threads per brick, one node each.
 // Rigids of a scene are staged in shared memory (posed at the scene's clock).
+// Grid update of node nid of node brick B (Eq. 3, contact, walls), clearing
+// the P2G accumulator; rigid impulses are summed into simp (shared).
+__device__ __forceinline__ void grid_node(const StepArgs& a, int B, int scene, int nid, int lane, const RigidCur* rig,
+                                          int nr, float* simp)
+{
+    const SceneDev sc = a.scenes[scene];
+    const int n = sc.n, nb = sc.nb, lb = B - sc.brick_base;
+    const int gi = (lb / (nb * nb)) * 4 + (nid >> 4);
+    const int gj = ((lb / nb) % nb) * 4 + ((nid >> 2) & 3);
+    const int gk = (lb % nb) * 4 + (nid & 3);
+    const int node = B * 64 + nid;
+    const float4 g = a.G[node];
+    a.G[node] = make_float4(0.f, 0.f, 0.f, 0.f);
+    float3 v = f3(0.f, 0.f, 0.f);
+    const float dxs = 1.0f / (float)n;
+    float dpr[kMaxRigids][3];
+    unsigned touched = 0;
+    if (g.x > 0.f) {
+        v = f3(g.y / g.x + a.dt * a.gravity[0], g.z / g.x + a.dt * a.gravity[1], g.w / g.x + a.dt * a.gravity[2]);
+        const float3 xI = f3(gi * dxs, gj * dxs, gk * dxs);
+        for (int r = 0; r < nr; ++r) {
+            float3 dp;
+            if (rigid_contact(rig[r], xI, g.x, v, dp)) {
+                touched |= 1u << r;
+                dpr[r][0] = dp.x; dpr[r][1] = dp.y; dpr[r][2] = dp.z;
+            }
+        }
+        const int lo = a.bound, hi = n - 1 - a.bound;
+        if (gi < lo) v.x = fmaxf(v.x, 0.f);
+        if (gi > hi) v.x = fminf(v.x, 0.f);
+        if (gj < lo) {
+            if (a.floor_sticky) v = f3(0.f, 0.f, 0.f);
+            else v.y = fmaxf(v.y, 0.f);
+        }
+        if (gj > hi) v.y = fminf(v.y, 0.f);
+        if (gk < lo) v.z = fmaxf(v.z, 0.f);
+        if (gk > hi) v.z = fminf(v.z, 0.f);
+    }
+    a.V[node] = make_float4(v.x, v.y, v.z, g.x);
+    if (nid == 0) {
+        a.brick_epoch[B] = a.epoch[scene];
+        // the histogram of the next substep starts from zero (the scan has
+        // read it; every non-empty brick is an active node brick)
+        a.sb.cnt[B] = 0;
+    }
+    // impulse on each rigid: -(node momentum change), linear and angular
+    for (int r = 0; r < nr; ++r) {
+        const bool on = (touched >> r) & 1u;
+        if (!__any_sync(kFull, on)) continue;
+        float val[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (on) {
+            const float d0 = -dpr[r][0], d1 = -dpr[r][1], d2 = -dpr[r][2];
+            const float r0 = gi * dxs - rig[r].c[0], r1 = gj * dxs - rig[r].c[1], r2 = gk * dxs - rig[r].c[2];
+            val[0] = d0; val[1] = d1; val[2] = d2;
+            val[3] = r1 * d2 - r2 * d1;
+            val[4] = r2 * d0 - r0 * d2;
+            val[5] = r0 * d1 - r1 * d0;
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            float x = val[c];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+            if (lane == 0) atomicAdd(&simp[r * 6 + c], x);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kGridThreads) k_grid(StepArgs a)
 {
     __shared__ RigidCur rig[kMaxRigids];
@@ -544,6 +612,12 @@ __global__ void __launch_bounds__(kGridThreads) k_grid(StepArgs a)
     for (int base = blockIdx.x * 4; base < n_nact; base += gridDim.x * 4) {
         const int item = base + grp;
         const int my_scene = item < n_nact ? a.sb.nact_scene[item] : -1;
+        const int my_nr = my_scene >= 0 ? a.scenes[my_scene].n_rigid : 0;
+        if (!__syncthreads_or(my_nr > 0)) {
+            // no rigid in any of the 4 bricks: no staging, no barriers
+            if (my_scene >= 0) grid_node(a, a.sb.nact_brick[item], my_scene, nid, lane, nullptr, 0, nullptr);
+            continue;
+        }
         if (nid == 0) s_scene[grp] = my_scene;
         bool done = my_scene < 0;
         __syncthreads();
@@ -574,69 +648,7 @@ __global__ void __launch_bounds__(kGridThreads) k_grid(StepArgs a)
             }
             if (!done && my_scene == target) {
                 done = true;
-                const int B = a.sb.nact_brick[item];
-                const SceneDev sc = a.scenes[target];
-                const int n = sc.n, nb = sc.nb, lb = B - sc.brick_base;
-                const int gi = (lb / (nb * nb)) * 4 + (nid >> 4);
-                const int gj = ((lb / nb) % nb) * 4 + ((nid >> 2) & 3);
-                const int gk = (lb % nb) * 4 + (nid & 3);
-                const int node = B * 64 + nid;
-                const float4 g = a.G[node];
-                a.G[node] = make_float4(0.f, 0.f, 0.f, 0.f);
-                float3 v = f3(0.f, 0.f, 0.f);
-                const float dxs = 1.0f / (float)n;
-                const int nr = s_nrig;
-                float dpr[kMaxRigids][3];
-                unsigned touched = 0;
-                if (g.x > 0.f) {
-                    v = f3(g.y / g.x + a.dt * a.gravity[0], g.z / g.x + a.dt * a.gravity[1], g.w / g.x + a.dt * a.gravity[2]);
-                    const float3 xI = f3(gi * dxs, gj * dxs, gk * dxs);
-                    for (int r = 0; r < nr; ++r) {
-                        float3 dp;
-                        if (rigid_contact(rig[r], xI, g.x, v, dp)) {
-                            touched |= 1u << r;
-                            dpr[r][0] = dp.x; dpr[r][1] = dp.y; dpr[r][2] = dp.z;
-                        }
-                    }
-                    const int lo = a.bound, hi = n - 1 - a.bound;
-                    if (gi < lo) v.x = fmaxf(v.x, 0.f);
-                    if (gi > hi) v.x = fminf(v.x, 0.f);
-                    if (gj < lo) {
-                        if (a.floor_sticky) v = f3(0.f, 0.f, 0.f);
-                        else v.y = fmaxf(v.y, 0.f);
-                    }
-                    if (gj > hi) v.y = fminf(v.y, 0.f);
-                    if (gk < lo) v.z = fmaxf(v.z, 0.f);
-                    if (gk > hi) v.z = fminf(v.z, 0.f);
-                }
-                a.V[node] = make_float4(v.x, v.y, v.z, g.x);
-                if (nid == 0) {
-                    a.brick_epoch[B] = a.epoch[target];
-                    // the histogram of the next substep starts from zero (the scan
-                    // has read it; every non-empty brick is an active node brick)
-                    a.sb.cnt[B] = 0;
-                }
-                // impulse on each rigid: -(node momentum change), linear and angular
-                for (int r = 0; r < nr; ++r) {
-                    const bool on = (touched >> r) & 1u;
-                    if (!__any_sync(kFull, on)) continue;
-                    float val[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                    if (on) {
-                        const float d0 = -dpr[r][0], d1 = -dpr[r][1], d2 = -dpr[r][2];
-                        const float r0 = gi * dxs - rig[r].c[0], r1 = gj * dxs - rig[r].c[1], r2 = gk * dxs - rig[r].c[2];
-                        val[0] = d0; val[1] = d1; val[2] = d2;
-                        val[3] = r1 * d2 - r2 * d1;
-                        val[4] = r2 * d0 - r0 * d2;
-                        val[5] = r0 * d1 - r1 * d0;
-                    }
-#pragma unroll
-                    for (int c = 0; c < 6; ++c) {
-                        float x = val[c];
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-                        if (lane == 0) atomicAdd(&simp[r * 6 + c], x);
-                    }
-                }
+                grid_node(a, a.sb.nact_brick[item], target, nid, lane, rig, s_nrig, simp);
             }
             __syncthreads();
             if (nid == 0 && my_scene == target) s_scene[grp] = -1;
@@ -661,7 +673,7 @@ struct G2POut {
     float x[3], v[3], C[9], t6[6];
 };
 
-__device__ __forceinline__ unsigned g2p_particle(const StepArgs& a, const SceneDev& sc, const float4* win, int p, int s,
+__device__ __forceinline__ unsigned g2p_particle(const StepArgs& a, const SceneDev& sc, const float4* lin, int p, int s,
                                                  int ox, int oy, int oz, G2POut& o)
 {
     const int cap = a.cap, n = sc.n;
@@ -672,32 +684,47 @@ __device__ __forceinline__ unsigned g2p_particle(const StepArgs& a, const SceneD
     float f[3], w[9];
     particle_weights(x0, x1, x2, n, bc, f, w);
     const int l0 = min(max(bc[0] - ox, 0), 3), l1 = min(max(bc[1] - oy, 0), 3), l2 = min(max(bc[2] - oz, 0), 3);
-    float v0 = 0.f, v1 = 0.f, v2 = 0.f;
-    float B[9];
+    // separable contraction over k, then j, then i of
+    //   v = sum W v_I,  B_rc = sum W v_I,r (o_c - f_c),  W = wx_i wy_j wz_k
+    const float* wx = w;
+    const float* wy = w + 3;
+    const float* wz = w + 6;
+    float wxd[3], wyd[3], wzd[3];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) B[i] = 0.f;
+    for (int q = 0; q < 3; ++q) {
+        wxd[q] = wx[q] * ((float)q - f[0]);
+        wyd[q] = wy[q] * ((float)q - f[1]);
+        wzd[q] = wz[q] * ((float)q - f[2]);
+    }
+    const float4* base = lin + (l0 * 36 + l1 * 6 + l2);
+    float A[3][3], Ay[3][3], Bz[3][3];  // [i][component]
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        const int wi = l0 + i;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) A[i][c] = Ay[i][c] = Bz[i][c] = 0.f;
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            const int wj = l1 + j;
-            const float wij = w[i] * w[3 + j];
-#pragma unroll
-            for (int k2 = 0; k2 < 3; ++k2) {
-                const int wk = l2 + k2;
-                const int sub = ((wi >> 2) << 2) | ((wj >> 2) << 1) | (wk >> 2);
-                const float4 g = win[sub * 64 + (wi & 3) * 16 + (wj & 3) * 4 + (wk & 3)];
-                const float W = wij * w[6 + k2];
-                const float g0 = W * g.x, g1 = W * g.y, g2 = W * g.z;
-                v0 += g0; v1 += g1; v2 += g2;
-                const float d0 = (float)i - f[0], d1 = (float)j - f[1], d2 = (float)k2 - f[2];
-                B[0] += g0 * d0; B[1] += g0 * d1; B[2] += g0 * d2;
-                B[3] += g1 * d0; B[4] += g1 * d1; B[5] += g1 * d2;
-                B[6] += g2 * d0; B[7] += g2 * d1; B[8] += g2 * d2;
-            }
+            const float4 g0 = base[i * 36 + j * 6], g1 = base[i * 36 + j * 6 + 1], g2 = base[i * 36 + j * 6 + 2];
+            const float ax = wz[0] * g0.x + wz[1] * g1.x + wz[2] * g2.x;
+            const float ay = wz[0] * g0.y + wz[1] * g1.y + wz[2] * g2.y;
+            const float az = wz[0] * g0.z + wz[1] * g1.z + wz[2] * g2.z;
+            const float bx = wzd[0] * g0.x + wzd[1] * g1.x + wzd[2] * g2.x;
+            const float by = wzd[0] * g0.y + wzd[1] * g1.y + wzd[2] * g2.y;
+            const float bz = wzd[0] * g0.z + wzd[1] * g1.z + wzd[2] * g2.z;
+            A[i][0] += wy[j] * ax; A[i][1] += wy[j] * ay; A[i][2] += wy[j] * az;
+            Ay[i][0] += wyd[j] * ax; Ay[i][1] += wyd[j] * ay; Ay[i][2] += wyd[j] * az;
+            Bz[i][0] += wy[j] * bx; Bz[i][1] += wy[j] * by; Bz[i][2] += wy[j] * bz;
         }
     }
+    float vv[3], B[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        vv[r] = wx[0] * A[0][r] + wx[1] * A[1][r] + wx[2] * A[2][r];
+        B[3 * r] = wxd[0] * A[0][r] + wxd[1] * A[1][r] + wxd[2] * A[2][r];
+        B[3 * r + 1] = wx[0] * Ay[0][r] + wx[1] * Ay[1][r] + wx[2] * Ay[2][r];
+        B[3 * r + 2] = wx[0] * Bz[0][r] + wx[1] * Bz[1][r] + wx[2] * Bz[2][r];
+    }
+    const float v0 = vv[0], v1 = vv[1], v2 = vv[2];
     // C = D^-1 sum N v (x_I - x_p)^T = 4/dx^2 * dx * B  (Eq. 9); x += dt v (Eq. 4)
     const float c4 = 4.0f * fn;
 #pragma unroll
@@ -746,10 +773,24 @@ __device__ __forceinline__ unsigned g2p_particle(const StepArgs& a, const SceneD
     return ebits;
 }
 
+// Copy the 6^3 window out of the 2x2x2 staged bricks into a linear array, so
+// that the 27 nodes of a particle sit at constant offsets.
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 768 / BLOCK) k_g2p(StepArgs a)
+__device__ __forceinline__ void linearize_window(const float4* vw, float4* lin)
+{
+    for (int t = threadIdx.x; t < kWinNodes; t += BLOCK) {
+        const int wi = t / 36, wj = (t / 6) % 6, wk = t % 6;
+        lin[t] = vw[(((wi >> 2) << 2) | ((wj >> 2) << 1) | (wk >> 2)) * 64 + (wi & 3) * 16 + (wj & 3) * 4 + (wk & 3)];
+    }
+}
+
+// MINB = CTAs per SM the registers must allow (768/BLOCK: 80 registers;
+// 1024/BLOCK: 64 registers with a few spills, more warps in flight).
+template <int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_g2p(StepArgs a)
 {
     __shared__ __align__(128) float4 vw[2][8 * 64];
+    __shared__ __align__(16) float4 lin[kWinNodes];
     __shared__ __align__(8) unsigned long long bar[2];
     __shared__ int s_item[2];
     const int tid = threadIdx.x;
@@ -766,6 +807,8 @@ __global__ void __launch_bounds__(BLOCK, 768 / BLOCK) k_g2p(StepArgs a)
         const SceneDev sc = a.scenes[scene];
         const int nb = sc.nb, lb = a.sb.act_brick[item] - sc.brick_base;
         const int ox = (lb / (nb * nb)) * 4, oy = ((lb / nb) % nb) * 4, oz = (lb % nb) * 4;
+        linearize_window<BLOCK>(vw[buf], lin);
+        __syncthreads();
         unsigned ebits = 0;
         for (int k0 = 0; k0 < count; k0 += BLOCK) {
             const int k = k0 + tid;
@@ -773,7 +816,7 @@ __global__ void __launch_bounds__(BLOCK, 768 / BLOCK) k_g2p(StepArgs a)
             int key = 0;
             if (valid) {
                 G2POut o;
-                ebits |= g2p_particle(a, sc, vw[buf], a.sb.perm[start + k], start + k, ox, oy, oz, o);
+                ebits |= g2p_particle(a, sc, lin, a.sb.perm[start + k], start + k, ox, oy, oz, o);
 #pragma unroll
                 for (int q = 0; q < 6; ++q) a.out.tau[(size_t)q * a.cap + start + k] = o.t6[q];
                 unsigned ood = 0;
@@ -808,6 +851,7 @@ constexpr int kW8 = 8, kW8Nodes = kW8 * kW8 * kW8;
 __global__ void __launch_bounds__(kFusedThreads, 4) k_g2p2g(StepArgs a)
 {
     __shared__ __align__(128) float4 vw[2][8 * 64];
+    __shared__ __align__(16) float4 lin[kWinNodes];
     __shared__ float rec[kRecFields][kFusedThreads];
     __shared__ float win[4][kW8Nodes];
     __shared__ short order[kFusedThreads];
@@ -835,6 +879,8 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_g2p2g(StepArgs a)
         const float fn = (float)n, dxs = 1.0f / fn;
         const float m = sc.m_p;
         const float kA = a.dt * sc.V0 * 4.0f * fn * fn;
+        linearize_window<kFusedThreads>(vw[buf], lin);
+        __syncthreads();
         unsigned ebits = 0;
         for (int k0 = 0; k0 < count; k0 += kFusedThreads) {
             const int k = k0 + tid;
@@ -842,7 +888,7 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_g2p2g(StepArgs a)
             int key = 0, my_cell = -1, my_rank = 0;
             if (valid) {
                 G2POut o;
-                ebits |= g2p_particle(a, sc, vw[buf], a.sb.perm[start + k], start + k, ox, oy, oz, o);
+                ebits |= g2p_particle(a, sc, lin, a.sb.perm[start + k], start + k, ox, oy, oz, o);
                 // P2G of the next substep at the new position
                 int bc[3];
                 float f[3], w[9];
@@ -1030,10 +1076,19 @@ cudaError_t launch_grid(const StepArgs& a, cudaStream_t s)
 
 cudaError_t launch_g2p(const StepArgs& a, cudaStream_t s)
 {
-    switch (a.g2p_threads) {
-    case 128: k_g2p<128><<<a.persistent_ctas, 128, 0, s>>>(a); break;
-    case 512: k_g2p<512><<<a.persistent_ctas, 512, 0, s>>>(a); break;
-    default: k_g2p<256><<<a.persistent_ctas, 256, 0, s>>>(a); break;
+    const int c = a.persistent_ctas;
+    if (a.g2p_regs64) {
+        switch (a.g2p_threads) {
+        case 128: k_g2p<128, 8><<<c, 128, 0, s>>>(a); break;
+        case 512: k_g2p<512, 2><<<c, 512, 0, s>>>(a); break;
+        default: k_g2p<256, 4><<<c, 256, 0, s>>>(a); break;
+        }
+    } else {
+        switch (a.g2p_threads) {
+        case 128: k_g2p<128, 6><<<c, 128, 0, s>>>(a); break;
+        case 512: k_g2p<512, 1><<<c, 512, 0, s>>>(a); break;
+        default: k_g2p<256, 3><<<c, 256, 0, s>>>(a); break;
+        }
     }
     return cudaGetLastError();
 }
@@ -1042,6 +1097,13 @@ cudaError_t launch_g2p2g(const StepArgs& a, cudaStream_t s)
 {
     k_g2p2g<<<a.fused_ctas, kFusedThreads, 0, s>>>(a);
     return cudaGetLastError();
+}
+
+int occupancy_grid()
+{
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_grid, kGridThreads, 0);
+    return b;
 }
 
 int occupancy_g2p2g()
@@ -1089,12 +1151,18 @@ int occupancy_p2g(int chunk)
     return b;
 }
 
-int occupancy_g2p(int threads)
+int occupancy_g2p(int threads, int regs64)
 {
     int b = 0;
-    if (threads == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<128>, 128, 0);
-    else if (threads == 512) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<512>, 512, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<256>, 256, 0);
+    if (regs64) {
+        if (threads == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<128, 8>, 128, 0);
+        else if (threads == 512) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<512, 2>, 512, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<256, 4>, 256, 0);
+    } else {
+        if (threads == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<128, 6>, 128, 0);
+        else if (threads == 512) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<512, 1>, 512, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<256, 3>, 256, 0);
+    }
     return b;
 }
 

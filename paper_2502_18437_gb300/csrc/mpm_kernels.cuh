@@ -51,14 +51,14 @@ struct StepArgs {
     int persistent_ctas;         // CTAs of the persistent G2P kernel
     int p2g_ctas, grid_ctas;     // CTAs of the persistent P2G and grid kernels
     int fused_ctas;              // CTAs of the fused G2P + P2G kernel
-    int p2g_chunk, g2p_threads;
+    int p2g_chunk, g2p_threads, g2p_regs64;
     int tau_valid;               // P2G reads the stored stress (else recomputes it from F)
 };
 
 constexpr int kStateFloats = 32;  // x3 v3 C9 F9 tau6 mu lam (+ int id)
 constexpr int kP2GThreads = 192;  // 64 cells x 3 node slices
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 8;
+constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
 cudaError_t launch_prepare(const StepArgs& a, const PState& st, cudaStream_t s);
@@ -68,6 +68,7 @@ cudaError_t launch_grid(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_g2p(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_g2p2g(const StepArgs& a, cudaStream_t s);
 int occupancy_g2p2g();
+int occupancy_grid();
 
 // state I/O helpers
 cudaError_t launch_gather_field(const PState& st, int cap, int p0, int np, int field, void* dst,
@@ -82,6 +83,6 @@ cudaError_t launch_scatter_field(const PState& st, int cap, int p0, int np, int 
 cudaError_t launch_read_grid(const float4* V, const int* brick_epoch, const int* epoch, const SceneDev* scenes,
                              int scene, int n, int brick_base, float* dst, cudaStream_t s);
 int occupancy_p2g(int chunk);
-int occupancy_g2p(int threads);
+int occupancy_g2p(int threads, int regs64);
 
 }  // namespace mpm

@@ -28,7 +28,7 @@ RIGID_TYPES = {"sphere": 0, "box": 1, "quad_slicer": 2, "segments": 3, "none": -
 FIELD = {"x": 1, "v": 2, "C": 4, "F": 8, "order": 16, "impulse": 32}
 FIELD_SHAPE = {"x": (3,), "v": (3,), "C": (3, 3), "F": (3, 3), "order": ()}
 OPT = {"use_graphs": 1, "launch_mode": 2, "p2g_threads": 3, "g2p_threads": 4, "ctas_per_sm": 5, "graph_chunk": 6,
-       "phase_timing": 7, "p2g_chunk": 8, "fused": 9}
+       "phase_timing": 7, "p2g_chunk": 8, "fused": 9, "g2p_regs64": 10}
 MAX_PTS = 64
 MAX_RIGIDS = 8
 EBIT = {"out_of_domain": 1, "nonfinite": 2, "inverted": 4, "timeout": 8, "internal": 16}
