@@ -51,6 +51,42 @@ def dist_env():
     return world, rank, local
 
 
+# ------------------------------------------------------------- replicas
+
+class Replicas:
+    """Host side of the replica mode: every rank simulates its own copy of the
+    workload (no data-path collective); ranks meet at barriers around the
+    timed region and the slowest rank's time is the job's time.  ``dist`` is
+    torch.distributed with an initialised process group, or None for one
+    process; ``device`` is where the reduction tensor lives (cuda for NCCL,
+    cpu for gloo); ``sync`` drains the device queue on each side of a barrier."""
+
+    def __init__(self, dist=None, device="cpu", sync=None):
+        self.dist, self.device, self.sync = dist, device, sync
+
+    def barrier(self):
+        if self.sync:
+            self.sync()
+        if self.dist:
+            self.dist.barrier()
+        if self.sync:
+            self.sync()
+
+    def max_over_ranks(self, x):
+        if not self.dist:
+            return x
+        import torch
+
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, ms):
+    """Units of all ranks per second, timed by the slowest rank (weak scaling)."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 # --------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -165,18 +201,8 @@ def run_ours(args):
     if args.autotune:
         sim.autotune(dt, 5)
 
-    def barrier():
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    def max_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    reps = Replicas(dist, device="cuda", sync=torch.cuda.synchronize)
+    barrier, max_over_ranks = reps.barrier, reps.max_over_ranks
 
     # ---- device-resident timed region (graph replay) -------------------
     for _ in range(args.warmup):
@@ -196,7 +222,7 @@ def run_ours(args):
     clk = clocks.stop()
     ms = max_over_ranks(ms)
     total_substeps = args.steps * SUBSTEPS_PER_STEP
-    value = world * N * total_substeps / (ms / 1e3)
+    value = whole_job_rate(world, N * total_substeps, ms)
     ms_per_step = ms / args.steps
 
     # ---- per-kernel durations (CUDA events around each phase) ---------------
@@ -259,7 +285,7 @@ def run_ours(args):
             e2e_step()
         barrier()
         e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3)
-        line["e2e"] = {"value": world * N * total_substeps / (e2e_ms / 1e3), "unit": UNIT,
+        line["e2e"] = {"value": whole_job_rate(world, N * total_substeps, e2e_ms), "unit": UNIT,
                        "h2d_bytes_per_step": 96 * N, "d2h_bytes_per_step": 96 * N,
                        "ms_per_step": e2e_ms / args.steps,
                        "what": "mpm_write_state(x,v,C,F from pinned host) + 10 substeps + mpm_read_state(x,v,C,F to pinned host)"}
