@@ -157,7 +157,7 @@ StepArgs step_args(mpm_ctx* c, float dt, int s0, int s1, const PState& in, const
     const int ti = c->g2p_threads == 128 ? 0 : c->g2p_threads == 512 ? 2 : 1;
     int& og = c->occ_g2p[c->g2p_regs64 ? 1 : 0][ti];
     if (!og) og = std::max(1, occupancy_g2p(c->g2p_threads, c->g2p_regs64));
-    int& op = c->occ_p2g[c->p2g_chunk == kP2GThreads ? 0 : 1];
+    int& op = c->occ_p2g[c->p2g_chunk / kP2GThreads - 2];
     if (!op) op = std::max(1, occupancy_p2g(c->p2g_chunk));
     if (!c->occ_grid) c->occ_grid = std::max(1, occupancy_grid());
     if (!c->occ_fused) c->occ_fused = std::max(1, occupancy_g2p2g());
@@ -318,6 +318,7 @@ extern "C" int mpm_create(const mpm_config* cfg, void* stream, mpm_ctx** out)
         c->own_stream = e == cudaSuccess;
     }
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e == cudaSuccess) e = prepare_p2g();
     const size_t nbk = (size_t)c->total_bricks;
     c->n_tiles_max = (int)((nbk + kScanTile - 1) / kScanTile);
     auto alloc = [&](void** p, size_t bytes) {
@@ -392,7 +393,8 @@ extern "C" int mpm_set_option(mpm_ctx* c, int option, int64_t value)
         if (value != kP2GThreads) return MPM_ERR_INVALID_ARGUMENT;
         break;
     case MPM_OPT_P2G_CHUNK:
-        if (value != kP2GThreads && value != 2 * kP2GThreads) return MPM_ERR_INVALID_ARGUMENT;
+        if (value != 2 * kP2GThreads && value != 3 * kP2GThreads && value != 4 * kP2GThreads)
+            return MPM_ERR_INVALID_ARGUMENT;
         c->p2g_chunk = (int)value;
         break;
     case MPM_OPT_G2P_THREADS:
@@ -821,13 +823,13 @@ extern "C" int mpm_autotune(mpm_ctx* c, float dt, int trial_substeps, float* bes
     if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
     int best[4] = {c->p2g_chunk, c->g2p_threads, c->ctas_per_sm, c->g2p_regs64};
     float best_ms = 3.4e38f;
-    const int chunks[2] = {kP2GThreads, 2 * kP2GThreads};
+    const int chunks[3] = {2 * kP2GThreads, 3 * kP2GThreads, 4 * kP2GThreads};
     const int threads[3] = {128, 256, 512};
     const int ctas[2] = {0, 2};
     const int T = trial_substeps + (trial_substeps & 1);
     const bool tau_valid0 = c->tau_valid;
     const bool graphs = c->use_graphs && !c->phase_timing;
-    for (int a = 0; a < 2 && ce == cudaSuccess && st == MPM_OK; ++a)
+    for (int a = 0; a < 3 && ce == cudaSuccess && st == MPM_OK; ++a)
         for (int b = 0; b < 3 && ce == cudaSuccess && st == MPM_OK; ++b)
             for (int r64 = 0; r64 < 2 && ce == cudaSuccess && st == MPM_OK; ++r64)
             for (int k = 0; k < 2 && ce == cudaSuccess && st == MPM_OK; ++k) {

@@ -56,7 +56,7 @@ struct mpm_ctx {
     // options
     int use_graphs = 1;
     int launch_mode = 0;
-    int p2g_chunk = mpm::kP2GThreads;
+    int p2g_chunk = 3 * mpm::kP2GThreads;
     int g2p_threads = 256;
     int g2p_regs64 = 1;
     int ctas_per_sm = 0;
@@ -65,7 +65,7 @@ struct mpm_ctx {
     int fused = 0;
     // occupancy (resident CTAs per SM) of each kernel variant on this device, 0 = not asked yet
     int occ_g2p[2][3] = {};
-    int occ_p2g[2] = {};
+    int occ_p2g[3] = {};
     int occ_grid = 0;
     int occ_fused = 0;
     std::vector<cudaEvent_t> phase_events;  // 5 per timed substep

@@ -248,35 +248,51 @@ __global__ void k_prepare(StepArgs a, PState st)
 
 // ------------------------------------------------------------------ P2G
 //
-// One CTA per active particle brick (4^3 cells, a 6^3-node window).  Per chunk
-// of up to CHUNK particles:
-//   A. one thread per particle: stress, weights and P2G coefficients into a
-//      record in shared memory; the chunk is counting-sorted by cell;
-//   B. thread (cell c, slice i) sums, in registers, the contributions of the
-//      particles of cell c to its 9 nodes c + (i, j, k): no atomics.
-// At the end of the brick every thread adds its 9 node sums into the shared
-// window (the 32 lanes of a warp hold 32 distinct cells of one slice, so a
-// warp never hits the same node twice), and the window is added to HBM with
-// one vector reduction per node.  Used for the first substep of a run (the
-// fused kernel below scatters every later substep).
+// One CTA per active particle brick (4^3 cells, a 6^3-node window), 192
+// threads.  Per pass over up to PER x 192 particles of the brick:
+//   A1. one thread per particle: base cell and rank inside the cell;
+//   (warp 0) the cells' particles are cut into at most 64 balanced work items
+//      (build_items), so that the lanes of a warp run loops of nearly equal
+//      length instead of as long as the warp's fullest cell;
+//   A2. stress, weights and P2G coefficients into a record in shared memory at
+//      slot base(warp) + (position in item) x 32 + lane of the item, so that
+//      the 32 lanes of a warp read 32 consecutive words in phase B (no bank
+//      conflicts); a pass whose two item warps need more than kP2GSlots slots
+//      falls back to cell-sorted slots;
+//   B.  thread (item, slice i) sums, in registers, the contributions of its
+//      item's particles to the 9 nodes cell + (i, j, k) and stages the sums;
+//   C.  thread (cell, slice i) adds the staged sums of its cell's items and
+//      adds them to slice i's copy of the 6^3 window: the 64 cells of a slice
+//      never write the same node at once, so no atomics are needed.
+// At the end of the brick the window is added to HBM with one vector reduction
+// per node.
 
-template <int CHUNK>
-__global__ void __launch_bounds__(kP2GThreads, CHUNK == kP2GThreads ? 5 : 4) k_p2g(StepArgs a)
+constexpr int kP2GSlots = 768;
+constexpr int kSliceNodes = 4 * 36;  // node planes x = slice .. slice + 3 of the 6^3 window
+constexpr int kStageFloats = 36 * 3 * 64;  // (9 nodes x 4 values) x 3 slices x 64 items
+static_assert(kStageFloats <= kItemRecFields * kP2GSlots, "the stage reuses the record slots");
+
+template <int PER>
+__global__ void __launch_bounds__(kP2GThreads, 4) k_p2g(StepArgs a)
 {
-    constexpr int PER = CHUNK / kP2GThreads;  // particles per thread per chunk
-    __shared__ float rec[kRecFields][CHUNK];
-    __shared__ short order[CHUNK];
+    constexpr int CHUNK = PER * kP2GThreads;
+    static_assert(CHUNK <= kP2GSlots, "a pass fits the record slots");
+    extern __shared__ __align__(16) float rec_dyn[];
+    float(*rec)[kP2GSlots] = reinterpret_cast<float(*)[kP2GSlots]>(rec_dyn);  // [kItemRecFields][kP2GSlots]
+    float* stage = rec_dyn;  // [36][3][64], written once phase B has read every record
     __shared__ int cell_cnt[64], cell_off[65];
-    __shared__ float win[4][kWinNodes];
-    __shared__ int s_item;
+    __shared__ short it_cell[64], it_beg[64], it_len[64], c_full[64], c_nf[64], c_rem[64];
+    // one window per slice (slice i writes node planes x = i..i+3 only): the
+    // slices' writes never collide
+    __shared__ float win[3][4][kSliceNodes];
+    __shared__ int s_item, s_nitems, s_len[3];
     const int tid = threadIdx.x;
-    const int cell = tid & 63, slice = tid >> 6;
-    const int cx = cell >> 4, cy = (cell >> 2) & 3, cz = cell & 3;
+    const int t = tid & 63, slice = tid >> 6;
     const int n_act = a.sb.counters[CTR_N_ACT];
     const int cap = a.cap;
     for (;;) {
         if (tid == 0) s_item = atomicAdd(&a.sb.counters[CTR_WORK_P2G], 1);
-        for (int t = tid; t < 4 * kWinNodes; t += kP2GThreads) (&win[0][0])[t] = 0.0f;
+        for (int q = tid; q < 12 * kSliceNodes; q += kP2GThreads) (&win[0][0][0])[q] = 0.0f;
         if (tid < 64) cell_cnt[tid] = 0;
         __syncthreads();
         const int item = s_item;
@@ -290,76 +306,152 @@ __global__ void __launch_bounds__(kP2GThreads, CHUNK == kP2GThreads ? 5 : 4) k_p
         const float m = sc.m_p;
         const float kA = a.dt * sc.V0 * 4.0f * fn * fn;
         unsigned ebits = 0;
-        float acc_w[9], acc_p[9][3];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) { acc_w[q] = 0.f; acc_p[q][0] = acc_p[q][1] = acc_p[q][2] = 0.f; }
 
         for (int c0 = 0; c0 < count; c0 += CHUNK) {
             const int cn = min(CHUNK, count - c0);
-            int my_cell[PER], my_rank[PER];
+            // A1: cell and rank of each particle of the pass
+            int pp[PER], pc[PER], pr[PER];
+            float px[PER][3];
 #pragma unroll
             for (int u = 0; u < PER; ++u) {
                 const int k = tid + u * kP2GThreads;
-                my_cell[u] = -1;
+                pc[u] = -1;
                 if (k < cn) {
                     const int p = a.sb.perm[start + c0 + k];
-                    int bc[3];
-                    float f[3], w[9];
-                    ebits |= particle_weights(a.in.x[p], a.in.x[cap + p], a.in.x[2 * cap + p], n, bc, f, w);
-                    float C[9], v[3], t6[6];
-#pragma unroll
-                    for (int q = 0; q < 9; ++q) C[q] = a.in.C[(size_t)q * cap + p];
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) v[q] = a.in.v[(size_t)q * cap + p];
-                    if (a.tau_valid) {
-#pragma unroll
-                        for (int q = 0; q < 6; ++q) t6[q] = a.in.tau[(size_t)q * cap + p];
-                    } else {
-                        // stress of the current F (after host writes, or seeding a fused run)
-                        float F[9];
-#pragma unroll
-                        for (int q = 0; q < 9; ++q) F[q] = a.in.F[(size_t)q * cap + p];
-                        const float mu = sc.pp_mat ? a.in.mu[p] : sc.mu, lam = sc.pp_mat ? a.in.lam[p] : sc.lam;
-                        ebits |= constitutive(a.model, 0, 0.f, mu, lam, F, t6);
-                    }
-                    float q3[3], Ad[9];
-                    p2g_coeffs(m, kA, dxs, v, C, t6, f, q3, Ad);
-                    put_record<CHUNK>(rec, k, w, q3, Ad);
-                    const int l0 = min(max(bc[0] - ox, 0), 3), l1 = min(max(bc[1] - oy, 0), 3), l2 = min(max(bc[2] - oz, 0), 3);
-                    my_cell[u] = (l0 * 4 + l1) * 4 + l2;
-                    my_rank[u] = atomicAdd(&cell_cnt[my_cell[u]], 1);
+                    pp[u] = p;
+                    px[u][0] = a.in.x[p];
+                    px[u][1] = a.in.x[cap + p];
+                    px[u][2] = a.in.x[2 * cap + p];
+                    int c[3];
+                    const unsigned ood = base_cell(px[u][0], n, c[0]) | base_cell(px[u][1], n, c[1]) |
+                                         base_cell(px[u][2], n, c[2]);
+                    if (ood) ebits |= MPM_EBIT_OUT_OF_DOMAIN;
+                    const int l0 = min(max(c[0] - ox, 0), 3), l1 = min(max(c[1] - oy, 0), 3),
+                              l2 = min(max(c[2] - oz, 0), 3);
+                    pc[u] = (l0 * 4 + l1) * 4 + l2;
+                    pr[u] = atomicAdd(&cell_cnt[pc[u]], 1);
                 }
             }
             __syncthreads();
-            scan_cells(cell_cnt, cell_off, tid);
+            if (tid < 32)
+                build_items(cell_cnt, cell_off, cn, it_cell, it_beg, it_len, &s_nitems, c_full, c_nf, c_rem, s_len);
             __syncthreads();
+            const int L = s_len[0], n_items = s_nitems;
+            const int rows0 = s_len[1], rows1 = s_len[2];  // record rows of the two item warps
+            const bool inter = 32 * (rows0 + rows1) <= kP2GSlots;
+            const float invL = 1.0f / (float)L;
+            if (tid < 64) cell_cnt[tid] = 0;  // counts of the next pass (last read before the barrier)
+            // A2: records at their slots
 #pragma unroll
-            for (int u = 0; u < PER; ++u)
-                if (my_cell[u] >= 0) order[cell_off[my_cell[u]] + my_rank[u]] = (short)(tid + u * kP2GThreads);
-            __syncthreads();
-            cell_accumulate<CHUNK>(rec, order, cell_off[cell], cell_off[cell + 1], slice, acc_w, acc_p);
-            __syncthreads();
-            if (tid < 64) cell_cnt[tid] = 0;
-            __syncthreads();
-        }
-        // node sums of this thread -> shared window
+            for (int u = 0; u < PER; ++u) {
+                if (pc[u] < 0) continue;
+                const int c = pc[u], r = pr[u], nf = c_nf[c];
+                int slot;
+                if (!inter) {
+                    slot = cell_off[c] + r;
+                } else {
+                    int ti, it;
+                    if (r < nf * L) {
+                        const int j = div_small(r, invL);
+                        ti = c_full[c] + j;
+                        it = r - j * L;
+                    } else {
+                        ti = c_rem[c];
+                        it = r - nf * L;
+                    }
+                    slot = (ti < 32 ? 0 : 32 * rows0) + it * 32 + (ti & 31);
+                }
+                const int p = pp[u];
+                int bc[3];
+                float f[3], w[9];
+                particle_weights(px[u][0], px[u][1], px[u][2], n, bc, f, w);
+                float C[9], v[3], t6[6];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            if (acc_w[q] != 0.f) {
-                const int node = (cx + slice) * 36 + (cy + q / 3) * 6 + (cz + q % 3);
-                atomicAdd(&win[0][node], acc_w[q] * m);
-                atomicAdd(&win[1][node], acc_p[q][0]);
-                atomicAdd(&win[2][node], acc_p[q][1]);
-                atomicAdd(&win[3][node], acc_p[q][2]);
+                for (int q = 0; q < 9; ++q) C[q] = a.in.C[(size_t)q * cap + p];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) v[q] = a.in.v[(size_t)q * cap + p];
+                if (a.tau_valid) {
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) t6[q] = a.in.tau[(size_t)q * cap + p];
+                } else {
+                    // stress of the current F (after host writes, or seeding a fused run)
+                    float F[9];
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) F[q] = a.in.F[(size_t)q * cap + p];
+                    const float mu = sc.pp_mat ? a.in.mu[p] : sc.mu, lam = sc.pp_mat ? a.in.lam[p] : sc.lam;
+                    ebits |= constitutive(a.model, 0, 0.f, mu, lam, F, t6);
+                }
+                float q3[3], Ad[9];
+                p2g_coeffs(m, kA, dxs, v, C, t6, f, q3, Ad);
+                put_item_record<kP2GSlots>(rec, slot, f, q3, Ad);
             }
+            __syncthreads();
+            // B: item sums in registers, then staged
+            float acc_w[9], acc_p[9][3];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) { acc_w[q] = 0.f; acc_p[q][0] = acc_p[q][1] = acc_p[q][2] = 0.f; }
+            if (t < n_items)
+                item_accumulate<kP2GSlots>(rec, inter ? (t < 32 ? 0 : 32 * rows0) + (t & 31) : it_beg[t], inter ? 32 : 1,
+                                           it_len[t], slice, acc_w, acc_p);
+            __syncthreads();
+            if (t < n_items) {
+                float* st = stage + slice * 64 + t;
+#pragma unroll
+                for (int q = 0; q < 9; ++q) {
+                    st[(4 * q) * 192] = acc_w[q] * m;
+                    st[(4 * q + 1) * 192] = acc_p[q][0];
+                    st[(4 * q + 2) * 192] = acc_p[q][1];
+                    st[(4 * q + 3) * 192] = acc_p[q][2];
+                }
+            }
+            __syncthreads();
+            // C: cell owners add their items' sums to their slice's window
+            {
+                const int c = t, nf = c_nf[c], f0 = c_full[c], pr_item = c_rem[c];
+                const int cx = c >> 4, cy = (c >> 2) & 3, cz = c & 3;
+                float sum[36];
+#pragma unroll
+                for (int q = 0; q < 36; ++q) sum[q] = 0.f;
+                const bool any = nf > 0 || pr_item >= 0;
+                for (int j = 0; j <= nf; ++j) {
+                    const int it = j < nf ? f0 + j : pr_item;
+                    if (it < 0) break;
+                    const float* st = stage + slice * 64 + it;
+#pragma unroll
+                    for (int q = 0; q < 36; ++q) sum[q] += st[q * 192];
+                }
+                // for one (j, k) the 64 cells of a slice write distinct nodes (the two
+                // warps of a slice cover disjoint x ranges); a node written for (j, k)
+                // is read for another (j, k) by a neighbour lane: warp barrier between
+                float(*w)[kSliceNodes] = win[slice];
+#pragma unroll
+                for (int q = 0; q < 9; ++q) {
+                    if (any) {
+                        const int node = cx * 36 + (cy + q / 3) * 6 + (cz + q % 3);
+                        w[0][node] += sum[4 * q];
+                        w[1][node] += sum[4 * q + 1];
+                        w[2][node] += sum[4 * q + 2];
+                        w[3][node] += sum[4 * q + 3];
+                    }
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        for (int t = tid; t < kWinNodes; t += kP2GThreads) {
-            const float mm = win[0][t];
-            if (mm == 0.0f) continue;
-            const int gi = ox + t / 36, gj = oy + (t / 6) % 6, gk = oz + t % 6;
+        for (int q = tid; q < kWinNodes; q += kP2GThreads) {
+            const int X = q / 36, yz = q % 36;
+            float s4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int sl = 0; sl < 3; ++sl) {
+                const int cx = X - sl;
+                if (cx < 0 || cx > 3) continue;
+#pragma unroll
+                for (int comp = 0; comp < 4; ++comp) s4[comp] += win[sl][comp][cx * 36 + yz];
+            }
+            if (s4[0] == 0.0f) continue;
+            const int gi = ox + X, gj = oy + yz / 6, gk = oz + yz % 6;
             if (gi >= n || gj >= n || gk >= n) continue;
-            red_add_v4(&a.G[node_index(sc, gi, gj, gk)], mm, win[1][t], win[2][t], win[3][t]);
+            red_add_v4(&a.G[node_index(sc, gi, gj, gk)], s4[0], s4[1], s4[2], s4[3]);
         }
         if (ebits) atomicOr(&a.err[scene], ebits);
         __syncthreads();
@@ -1061,10 +1153,26 @@ cudaError_t launch_sort(const StepArgs& a, cudaStream_t s, bool write_perm)
     return cudaGetLastError();
 }
 
+template <int PER>
+static constexpr size_t p2g_dyn_smem() { return sizeof(float) * kItemRecFields * kP2GSlots; }
+
+cudaError_t prepare_p2g()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_p2g<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2g_dyn_smem<2>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_p2g<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2g_dyn_smem<3>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_p2g<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2g_dyn_smem<4>());
+    return e;
+}
+
 cudaError_t launch_p2g(const StepArgs& a, cudaStream_t s)
 {
-    if (a.p2g_chunk == 2 * kP2GThreads) k_p2g<2 * kP2GThreads><<<a.p2g_ctas, kP2GThreads, 0, s>>>(a);
-    else k_p2g<kP2GThreads><<<a.p2g_ctas, kP2GThreads, 0, s>>>(a);
+    switch (a.p2g_chunk) {
+    case 2 * kP2GThreads: k_p2g<2><<<a.p2g_ctas, kP2GThreads, p2g_dyn_smem<2>(), s>>>(a); break;
+    case 4 * kP2GThreads: k_p2g<4><<<a.p2g_ctas, kP2GThreads, p2g_dyn_smem<4>(), s>>>(a); break;
+    default: k_p2g<3><<<a.p2g_ctas, kP2GThreads, p2g_dyn_smem<3>(), s>>>(a); break;
+    }
     return cudaGetLastError();
 }
 
@@ -1146,8 +1254,12 @@ cudaError_t launch_read_grid(const float4* V, const int* brick_epoch, const int*
 int occupancy_p2g(int chunk)
 {
     int b = 0;
-    if (chunk == 2 * kP2GThreads) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_p2g<2 * kP2GThreads>, kP2GThreads, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_p2g<kP2GThreads>, kP2GThreads, 0);
+    if (chunk == 2 * kP2GThreads)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_p2g<2>, kP2GThreads, p2g_dyn_smem<2>());
+    else if (chunk == 4 * kP2GThreads)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_p2g<4>, kP2GThreads, p2g_dyn_smem<4>());
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_p2g<3>, kP2GThreads, p2g_dyn_smem<3>());
     return b;
 }
 

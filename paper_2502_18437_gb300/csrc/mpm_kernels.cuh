@@ -64,6 +64,7 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 cudaError_t launch_prepare(const StepArgs& a, const PState& st, cudaStream_t s);
 cudaError_t launch_sort(const StepArgs& a, cudaStream_t s, bool write_perm = true);
 cudaError_t launch_p2g(const StepArgs& a, cudaStream_t s);
+cudaError_t prepare_p2g();  // shared-memory opt-in of the P2G variants (once per device, before any launch)
 cudaError_t launch_grid(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_g2p(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_g2p2g(const StepArgs& a, cudaStream_t s);

@@ -206,6 +206,165 @@ __device__ __forceinline__ void scan_cells(const int* cell_cnt, int* cell_off, i
     }
 }
 
+// floor(y / L) for 0 <= y < 2^22 from one single-precision product with
+// inv = 1/L: the exact quotient (y + 0.5)/L lies at least 0.5/L away from an
+// integer, which bounds the rounding error of the product from above.
+__device__ __forceinline__ int div_small(int y, float inv) { return (int)(((float)y + 0.5f) * inv); }
+
+// Work items of one P2G pass.  The particles of each cell (contiguous in the
+// cell-sorted order) are cut into items of at most L particles, L being the
+// smallest length that gives at most 64 items; items of length L come first,
+// then the shorter remainders, longest first (eight length classes), so that
+// the 32 lanes of a warp run loops of nearly the same length.  Called by warp
+// 0 once cell_cnt holds the pass's per-cell counts (cn <= 4095 particles);
+// writes cell_off (exclusive scan of cell_cnt, 65 entries), the item table
+// (cell, first position in the cell-sorted order, length), the item count, L,
+// per cell the index of its first full item, its number of full items and the
+// index of its remainder item (-1: none), and s_len = {L, longest item among
+// items 0..31, longest among items 32..63}.
+__device__ __forceinline__ void build_items(const int* cell_cnt, int* cell_off, int cn, short* it_cell, short* it_beg,
+                                            short* it_len, int* n_items, short* c_full, short* c_nf, short* c_rem,
+                                            int* s_len)
+{
+    const int lane = threadIdx.x & 31;
+    const int ca = 2 * lane, cb = ca + 1;
+    const int ka = cell_cnt[ca], kb = cell_cnt[cb];
+    const int kmax = __reduce_max_sync(kFull, max(ka, kb));
+    // smallest L in [L0, max(L0, kmax)] with sum_c ceil(k_c / L) <= 64 (the upper
+    // end always qualifies: every cell is then one item at most)
+    int lo = max(1, (cn + 63) >> 6), hi = max(lo, kmax);
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const float inv = 1.0f / (float)mid;
+        const int items =
+            __reduce_add_sync(kFull, div_small(ka + mid - 1, inv) + div_small(kb + mid - 1, inv));
+        if (items <= 64) hi = mid;
+        else lo = mid + 1;
+    }
+    const int L = lo;
+    const float inv = 1.0f / (float)L;
+    const int nfa = div_small(ka, inv), nfb = div_small(kb, inv);
+    const int ra = ka - nfa * L, rb = kb - nfb * L;
+    // one scan of (count, full items) packed in 16-bit halves
+    const int own = (ka + kb) | ((nfa + nfb) << 16);
+    int incl = own;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += t;
+    }
+    const int excl = incl - own;
+    const int offa = excl & 0xffff, offb = offa + ka;
+    const int fa = excl >> 16, fb = fa + nfa;
+    const int n_full = __shfl_sync(kFull, incl, 31) >> 16;
+    cell_off[ca] = offa;
+    cell_off[cb] = offb;
+    if (lane == 31) cell_off[64] = incl & 0xffff;
+    // remainders in eight length classes, longest class first, cell order inside
+    const int ga = ra > 0 ? div_small(8 * (L - ra), inv) : 8, gb = rb > 0 ? div_small(8 * (L - rb), inv) : 8;
+    const unsigned lt = (1u << lane) - 1u;
+    int pa = -1, pb = -1, base = n_full;
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+        const unsigned ma = __ballot_sync(kFull, ga == g), mb = __ballot_sync(kFull, gb == g);
+        if (ga == g) pa = base + __popc(ma & lt) + __popc(mb & lt);
+        if (gb == g) pb = base + __popc(ma & (lt | (1u << lane))) + __popc(mb & lt);
+        base += __popc(ma) + __popc(mb);
+    }
+    for (int j = 0; j < nfa; ++j) {
+        it_cell[fa + j] = (short)ca;
+        it_beg[fa + j] = (short)(offa + j * L);
+        it_len[fa + j] = (short)L;
+    }
+    for (int j = 0; j < nfb; ++j) {
+        it_cell[fb + j] = (short)cb;
+        it_beg[fb + j] = (short)(offb + j * L);
+        it_len[fb + j] = (short)L;
+    }
+    if (pa >= 0) {
+        it_cell[pa] = (short)ca;
+        it_beg[pa] = (short)(offa + nfa * L);
+        it_len[pa] = (short)ra;
+    }
+    if (pb >= 0) {
+        it_cell[pb] = (short)cb;
+        it_beg[pb] = (short)(offb + nfb * L);
+        it_len[pb] = (short)rb;
+    }
+    c_full[ca] = (short)fa;
+    c_full[cb] = (short)fb;
+    c_nf[ca] = (short)nfa;
+    c_nf[cb] = (short)nfb;
+    c_rem[ca] = (short)pa;
+    c_rem[cb] = (short)pb;
+    __syncwarp();
+    // longest item of each group of 32 (the record rows of that warp)
+    const int r0 = __reduce_max_sync(kFull, lane < base ? (int)it_len[lane] : 0);
+    const int r1 = __reduce_max_sync(kFull, lane + 32 < base ? (int)it_len[lane + 32] : 0);
+    if (lane == 31) {
+        *n_items = base;
+        s_len[0] = L;
+        s_len[1] = r0;
+        s_len[2] = r1;
+    }
+}
+
+// Record of one particle for the item schedule: fractional offsets f (3),
+// q (3) and Ad (9) of p2g_coeffs; the weights are recomputed in phase B.
+constexpr int kItemRecFields = 15;
+
+template <int N>
+__device__ __forceinline__ void put_item_record(float (*rec)[N], int k, const float f[3], const float q[3],
+                                                const float Ad[9])
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i) rec[i][k] = f[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) rec[3 + i][k] = q[i];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) rec[6 + i][k] = Ad[i];
+}
+
+// Phase B of the item schedule: thread (item, slice) adds the contributions of
+// the item's particles, whose records sit at slots slot0, slot0 + stride, ...,
+// to the 9 nodes cell + (slice, j, k) in registers.  The weights follow the
+// quadratic B-spline of bspline(): slice i needs w_i(f_x) only, written as
+// alpha + beta (f - gamma)^2.
+template <int N>
+__device__ __forceinline__ void item_accumulate(const float (*rec)[N], int slot0, int stride, int len, int slice,
+                                                float acc_w[9], float acc_p[9][3])
+{
+    const float si = (float)slice;
+    const float gam = slice == 0 ? 1.5f : (slice == 1 ? 1.0f : 0.5f);
+    const float bet = slice == 1 ? -1.0f : 0.5f, alp = slice == 1 ? 0.75f : 0.0f;
+    int k = slot0;
+    for (int j = 0; j < len; ++j, k += stride) {
+        const float fx = rec[0][k], fy = rec[1][k], fz = rec[2][k];
+        const float dxw = fx - gam;
+        const float wi = __fmaf_rn(bet * dxw, dxw, alp);
+        float wy[3], wz[3];
+        bspline(fy, wy);
+        bspline(fz, wz);
+        const float r0 = rec[3][k] + si * rec[6][k], r1 = rec[4][k] + si * rec[9][k], r2 = rec[5][k] + si * rec[12][k];
+        const float a01 = rec[7][k], a11 = rec[10][k], a21 = rec[13][k];
+        const float a02 = rec[8][k], a12 = rec[11][k], a22 = rec[14][k];
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) {
+            const float wij = wi * wy[jj];
+            const float s0 = r0 + a01 * jj, s1 = r1 + a11 * jj, s2 = r2 + a21 * jj;
+#pragma unroll
+            for (int kk = 0; kk < 3; ++kk) {
+                const float W = wij * wz[kk];
+                const int q = jj * 3 + kk;
+                acc_w[q] += W;
+                acc_p[q][0] += W * (s0 + a02 * kk);
+                acc_p[q][1] += W * (s1 + a12 * kk);
+                acc_p[q][2] += W * (s2 + a22 * kk);
+            }
+        }
+    }
+}
+
 // Global node index of node (gi, gj, gk) of a scene (brick layout).
 __device__ __forceinline__ int node_index(const SceneDev& sc, int gi, int gj, int gk)
 {

@@ -145,11 +145,37 @@ def test_sort_by_brick_order():
     assert np.array_equal(key[order], key[perm])  # identical key sequence (same bricks, same offsets)
 
 
+def dense_bricks_scene():
+    """Bricks far above the P2G pass size and single cells far above the mean:
+    1,700 particles in one 4^3-cell brick, 400 in one cell, 100 scattered."""
+    n = 32
+    dx = 1.0 / n
+    g = np.random.default_rng(41)
+    brick = (4.5 + 4.0 * g.random((1700, 3))) * dx   # base cells 4..7: one brick
+    cell = (10.5 + g.random((400, 3))) * dx          # base cell (10, 10, 10)
+    sparse = (6.0 + 18.0 * g.random((100, 3))) * dx
+    x = np.concatenate([brick, cell, sparse])
+    return W._scene(n, x, np.zeros_like(x), 1e4, 0.3, rho=1.0, V0=(dx / 2) ** 3, model="fixed_corotated",
+                    dt=1e-4, substeps=1, name="dense_bricks")
+
+
+@pytest.mark.parametrize("chunk", [384, 576, 768])
+def test_p2g_dense_bricks_and_heavy_cells(chunk):
+    # several P2G passes per brick, items cut from a 400-particle cell
+    sc = dense_bricks_scene()
+    v, C, F = perturbed(sc, seed=12)
+    x, v, C, F, out = gpu_one_step(sc, v, C, F, p2g_chunk=chunk)
+    st, gm, gv, err, _ = oracle_one_step(sc, x, v, C, F)
+    assert err == 0
+    check_fields(sc, out, st, Scales(sc, F))
+    check_grid(sc, out, gm, gv, Scales(sc, F))
+
+
 def test_graph_direct_and_looped_agree():
     sc = W.tissue_slab(cells=(32, 6, 32), lo=(0.3, 0.2, 0.3), size=(0.4, 0.08, 0.4), n=32, substeps=20)
     outs = []
     for opts in ({"use_graphs": 1}, {"use_graphs": 0}, {"launch_mode": 1}, {"fused": 0},
-                 {"fused": 0, "p2g_chunk": 192}):
+                 {"fused": 0, "p2g_chunk": 384}, {"fused": 0, "p2g_chunk": 768}):
         with mpm.from_workload(sc) as sim:
             for k, v in opts.items():
                 sim.set_option(k, v)
