@@ -258,7 +258,7 @@ static void free_ctx(mpm_ctx* c)
     mpm_tape_free(c);
     clear_graphs(c);
     for (int i = 0; i < 2; ++i) cudaFree(c->state_mem[i]);
-    void* bufs[] = {c->sb.key, c->sb.rank, c->sb.perm, c->sb.cnt, c->sb.off, c->sb.act_brick, c->sb.act_start,
+    void* bufs[] = {c->sb.key, c->sb.rank, c->sb.perm, c->sb.cnt, c->sb.nflag, c->sb.off, c->sb.act_brick, c->sb.act_start,
                     c->sb.act_count, c->sb.act_scene, c->sb.nact_brick, c->sb.nact_scene, c->sb.counters,
                     c->sb.tile_status, c->sb.tile_agg, c->sb.tile_incl, c->G, c->V, c->brick_epoch,
                     c->d_scenes, c->d_rigids, c->d_impulse, c->d_err, c->d_time, c->d_epoch, c->d_stage};
@@ -329,6 +329,7 @@ extern "C" int mpm_create(const mpm_config* cfg, void* stream, mpm_ctx** out)
     alloc((void**)&c->sb.rank, sizeof(int) * c->cap);
     alloc((void**)&c->sb.perm, sizeof(int) * c->cap);
     alloc((void**)&c->sb.cnt, sizeof(int) * nbk);
+    alloc((void**)&c->sb.nflag, sizeof(int) * nbk);
     alloc((void**)&c->sb.off, sizeof(int) * nbk);
     alloc((void**)&c->sb.act_brick, sizeof(int) * nbk);
     alloc((void**)&c->sb.act_start, sizeof(int) * nbk);
@@ -353,6 +354,7 @@ extern "C" int mpm_create(const mpm_config* cfg, void* stream, mpm_ctx** out)
     if (e == cudaSuccess) {
         for (int i = 0; i < 2; ++i) c->st[i] = state_view(c->state_mem[i], c->cap);
         cudaMemsetAsync(c->sb.cnt, 0, sizeof(int) * nbk, c->stream);
+        cudaMemsetAsync(c->sb.nflag, 0, sizeof(int) * nbk, c->stream);
         cudaMemsetAsync(c->sb.counters, 0, sizeof(int) * CTR_COUNT, c->stream);
         cudaMemsetAsync(c->sb.tile_status, 0, sizeof(unsigned) * c->n_tiles_max, c->stream);
         cudaMemsetAsync(c->G, 0, sizeof(float4) * nbk * 64, c->stream);
@@ -796,14 +798,15 @@ extern "C" int mpm_autotune(mpm_ctx* c, float dt, int trial_substeps, float* bes
     // snapshot everything a substep changes
     const size_t sbytes = state_bytes(c->cap);
     const size_t nbk = (size_t)c->total_bricks;
-    const size_t total = sbytes + 2 * sizeof(int) * c->cap + sizeof(int) * nbk * 2 +
+    const size_t total = sbytes + 2 * sizeof(int) * c->cap + sizeof(int) * nbk * 3 +
                          (sizeof(double) + sizeof(int) + sizeof(unsigned) + sizeof(double) * kMaxRigids * 6) * c->n_scenes;
     char* snap = nullptr;
     MPM_CK(cudaMalloc(&snap, total));
     struct Item { void* live; size_t bytes; };
     const int cur0 = c->cur;
     Item items[] = {{c->state_mem[cur0], sbytes}, {c->sb.key, sizeof(int) * c->cap}, {c->sb.rank, sizeof(int) * c->cap},
-                    {c->sb.cnt, sizeof(int) * nbk}, {c->brick_epoch, sizeof(int) * nbk},
+                    {c->sb.cnt, sizeof(int) * nbk}, {c->sb.nflag, sizeof(int) * nbk},
+                    {c->brick_epoch, sizeof(int) * nbk},
                     {c->d_time, sizeof(double) * c->n_scenes}, {c->d_epoch, sizeof(int) * c->n_scenes},
                     {c->d_err, sizeof(unsigned) * c->n_scenes},
                     {c->d_impulse, sizeof(double) * kMaxRigids * 6 * c->n_scenes}};

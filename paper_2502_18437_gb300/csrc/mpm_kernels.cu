@@ -71,16 +71,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(StepArgs a)
         if (b < end) {
             while (s + 1 < a.r.s1 && b >= a.scenes[s + 1].brick_base) ++s;
             sc[k] = s;
-            const int nb = a.scenes[s].nb, lb = b - a.scenes[s].brick_base;
-            const int bz = lb % nb, by = (lb / nb) % nb, bx = lb / (nb * nb);
-            c[k] = __ldg(&sb.cnt[b]);
-            bool nact = c[k] > 0;
-#pragma unroll
-            for (int o = 1; o < 8; ++o) {
-                const int ox = o >> 2, oy = (o >> 1) & 1, oz = o & 1;
-                if (bx >= ox && by >= oy && bz >= oz)
-                    nact |= __ldg(&sb.cnt[b - (ox * nb + oy) * nb - oz]) > 0;
-            }
+            c[k] = __ldcg(&sb.cnt[b]);
+            const int flag = __ldcg(&sb.nflag[b]);
+            if (flag) sb.nflag[b] = 0;  // consumed
+            const bool nact = c[k] > 0 || flag != 0;
             if (c[k] > 0) pf |= 1u << k;
             if (nact) nf |= 1u << k;
             local.x += c[k];
@@ -223,7 +217,7 @@ __global__ void k_prepare(StepArgs a, PState st)
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = a.r.p0 + g;
     const bool valid = g < a.r.np;
-    int key = 0, scene = -1;
+    int key = 0, scene = a.r.s0;
     unsigned ebits = 0;
     if (valid) {
         int lo = a.r.s0, hi = a.r.s1 - 1;
@@ -233,12 +227,14 @@ __global__ void k_prepare(StepArgs a, PState st)
             else hi = mid - 1;
         }
         scene = lo;
-        const SceneDev sc = a.scenes[scene];
+    }
+    const SceneDev sc = a.scenes[scene];
+    if (valid) {
         unsigned ood = 0;
         key = brick_key(sc, st.x[i], st.x[a.cap + i], st.x[2 * a.cap + i], ood);
         if (ood) ebits |= MPM_EBIT_OUT_OF_DOMAIN;
     }
-    const int rank = aggregated_rank(a.sb.cnt, key, valid);
+    const int rank = aggregated_rank_mark(a.sb.cnt, a.sb.nflag, sc, key, valid);
     if (valid) {
         a.sb.key[i] = key;
         a.sb.rank[i] = rank;
@@ -915,7 +911,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_g2p(StepArgs a)
                 key = brick_key(sc, o.x[0], o.x[1], o.x[2], ood);
                 if (ood && !(ebits & MPM_EBIT_NONFINITE)) ebits |= MPM_EBIT_OUT_OF_DOMAIN;
             }
-            const int rank = aggregated_rank(a.sb.cnt, key, valid);
+            const int rank = aggregated_rank_mark(a.sb.cnt, a.sb.nflag, sc, key, valid);
             if (valid) {
                 a.sb.key[start + k] = key;
                 a.sb.rank[start + k] = rank;
@@ -1025,7 +1021,7 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_g2p2g(StepArgs a)
                             }
                 }
             }
-            const int rank = aggregated_rank(a.sb.cnt, key, valid);
+            const int rank = aggregated_rank_mark(a.sb.cnt, a.sb.nflag, sc, key, valid);
             if (valid) {
                 a.sb.key[start + k] = key;
                 a.sb.rank[start + k] = rank;

@@ -16,6 +16,8 @@ struct SortBufs {
     int* rank;      // [cap] rank of the particle within its brick
     int* perm;      // [cap] sorted slot -> storage index
     int* cnt;       // [bricks] particles per brick (next substep)
+    int* nflag;     // [bricks] node brick touched by a particle brick's stencil (set by the
+                    // key producers, consumed and cleared by the scan)
     int* off;       // [bricks] first slot of each active brick
     int* act_brick; // [bricks] active particle bricks
     int* act_start;

@@ -110,6 +110,37 @@ __device__ __forceinline__ int aggregated_rank(int* cnt, int key, bool valid)
     return rank;
 }
 
+// aggregated_rank that also marks, for the first warp to add particles to a
+// brick in this substep, the brick and its 7 upper neighbours (+1 in any subset
+// of the axes) as node bricks the scan must activate: a particle's 3-node
+// stencil reaches at most 2 nodes past its base cell, i.e. into the next brick.
+__device__ __forceinline__ int aggregated_rank_mark(int* cnt, int* nflag, const SceneDev& sc, int key, bool valid)
+{
+    const unsigned active = __ballot_sync(kFull, valid);
+    int rank = 0;
+    const unsigned peers = __match_any_sync(kFull, valid ? key : -1) & active;
+    if (valid) {
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (lane == leader) {
+            base = atomicAdd(&cnt[key], __popc(peers));
+            if (base == 0) {
+                const int nb = sc.nb, lb = key - sc.brick_base;
+                const int bx = lb / (nb * nb), by = (lb / nb) % nb, bz = lb % nb;
+#pragma unroll
+                for (int o = 0; o < 8; ++o) {
+                    const int ex = bx + (o >> 2), ey = by + ((o >> 1) & 1), ez = bz + (o & 1);
+                    if (ex < nb && ey < nb && ez < nb) nflag[sc.brick_base + (ex * nb + ey) * nb + ez] = 1;
+                }
+            }
+        }
+        base = __shfl_sync(peers, base, leader);
+        rank = base + __popc(peers & ((1u << lane) - 1u));
+    }
+    return rank;
+}
+
 // ------------------------------------------------------ transfer helpers
 
 constexpr int kRecFields = 21;  // w0[3] w1[3] w2[3] q[3] Ad[9]
