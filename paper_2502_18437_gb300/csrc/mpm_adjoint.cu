@@ -629,9 +629,10 @@ int mpm_tape_record_substep(mpm_ctx* c, float dt)
     a.tau_valid = c->tau_valid;
     int st;
     if ((st = status_from_cuda(launch_sort(a, c->stream)))) return st;
+    MPM_CKA(launch_p2g(a, c->stream));
+    // the permutation G2P uses (P2G leaves it in cell order inside each pass)
     MPM_CKA(cudaMemcpyAsync(t->perms + (size_t)j * c->cap + a.r.p0, c->sb.perm + a.r.p0, sizeof(int) * a.r.np,
                             cudaMemcpyDeviceToDevice, c->stream));
-    MPM_CKA(launch_p2g(a, c->stream));
     MPM_CKA(launch_grid(a, c->stream));
     MPM_CKA(launch_g2p(a, c->stream));
     c->tau_valid = true;
@@ -710,6 +711,7 @@ extern "C" int mpm_backward(mpm_ctx* c, const float* dLdx, const float* dLdv, fl
         for (int j = j0; j < j1 - 1; ++j) {
             StepArgs a = step_args(c, t->dts[j], 0, c->n_scenes, seg_state(j - j0), seg_state(j - j0 + 1));
             a.tau_valid = 0;
+            a.cell_order = 0;  // the recorded permutation is already the one G2P used
             if ((st = sort_with_perm(c, a, seg_state(j - j0), t->perms + (size_t)j * cap))) return st;
             MPM_CKA(launch_p2g(a, c->stream));
             MPM_CKA(launch_grid(a, c->stream));
@@ -719,6 +721,7 @@ extern "C" int mpm_backward(mpm_ctx* c, const float* dLdx, const float* dLdv, fl
         for (int j = j1 - 1; j >= j0; --j) {
             StepArgs a = step_args(c, t->dts[j], 0, c->n_scenes, seg_state(j - j0), seg_state(j - j0));
             a.tau_valid = 0;
+            a.cell_order = 0;
             if ((st = sort_with_perm(c, a, seg_state(j - j0), t->perms + (size_t)j * cap))) return st;
             MPM_CKA(launch_p2g(a, c->stream));
             MPM_CKA(launch_grid(a, c->stream));

@@ -168,6 +168,7 @@ StepArgs step_args(mpm_ctx* c, float dt, int s0, int s1, const PState& in, const
     a.fused_ctas = c->num_sms * cap_occ(c, c->occ_fused);
     a.p2g_chunk = c->p2g_chunk;
     a.g2p_threads = c->g2p_threads;
+    a.cell_order = 1;
     return a;
 }
 

@@ -251,10 +251,13 @@ __global__ void k_prepare(StepArgs a, PState st)
 //      (build_items), so that the lanes of a warp run loops of nearly equal
 //      length instead of as long as the warp's fullest cell;
 //   A2. stress, weights and P2G coefficients into a record in shared memory at
-//      slot base(warp) + (position in item) x 32 + lane of the item, so that
-//      the 32 lanes of a warp read 32 consecutive words in phase B (no bank
-//      conflicts); a pass whose two item warps need more than kP2GSlots slots
-//      falls back to cell-sorted slots;
+//      slot base(warp) + (position in item) x 33 + lane of the item, so that
+//      the 32 lanes of a warp read 32 consecutive words in phase B and the
+//      particles of one item (consecutive lanes here when the input is in cell
+//      order) write to different banks; a pass whose two item warps need more
+//      than kP2GSlots slots falls back to cell-sorted slots.  The pass's slots
+//      of the permutation are rewritten in cell order (cell_order), so that G2P
+//      gathers a warp's 27-node stencils from a few neighbouring cells;
 //   B.  thread (item, slice i) sums, in registers, the contributions of its
 //      item's particles to the 9 nodes cell + (i, j, k) and stages the sums;
 //   C.  thread (cell, slice i) adds the staged sums of its cell's items and
@@ -263,7 +266,8 @@ __global__ void k_prepare(StepArgs a, PState st)
 // At the end of the brick the window is added to HBM with one vector reduction
 // per node.
 
-constexpr int kP2GSlots = 768;
+constexpr int kP2GSlotPitch = 33;  // 32 lanes + 1: rows of one item fall in different banks
+constexpr int kP2GSlots = 24 * kP2GSlotPitch;
 constexpr int kSliceNodes = 4 * 36;  // node planes x = slice .. slice + 3 of the 6^3 window
 constexpr int kStageFloats = 36 * 3 * 64;  // (9 nodes x 4 values) x 3 slices x 64 items
 static_assert(kStageFloats <= kItemRecFields * kP2GSlots, "the stage reuses the record slots");
@@ -334,7 +338,7 @@ __global__ void __launch_bounds__(kP2GThreads, 4) k_p2g(StepArgs a)
             __syncthreads();
             const int L = s_len[0], n_items = s_nitems;
             const int rows0 = s_len[1], rows1 = s_len[2];  // record rows of the two item warps
-            const bool inter = 32 * (rows0 + rows1) <= kP2GSlots;
+            const bool inter = kP2GSlotPitch * (rows0 + rows1) <= kP2GSlots;
             const float invL = 1.0f / (float)L;
             if (tid < 64) cell_cnt[tid] = 0;  // counts of the next pass (last read before the barrier)
             // A2: records at their slots
@@ -342,6 +346,9 @@ __global__ void __launch_bounds__(kP2GThreads, 4) k_p2g(StepArgs a)
             for (int u = 0; u < PER; ++u) {
                 if (pc[u] < 0) continue;
                 const int c = pc[u], r = pr[u], nf = c_nf[c];
+                // the pass's slots in cell order: G2P then reads (and stores) the
+                // particles of a warp from a few neighbouring cells
+                if (a.cell_order) a.sb.perm[start + c0 + cell_off[c] + r] = pp[u];
                 int slot;
                 if (!inter) {
                     slot = cell_off[c] + r;
@@ -355,7 +362,7 @@ __global__ void __launch_bounds__(kP2GThreads, 4) k_p2g(StepArgs a)
                         ti = c_rem[c];
                         it = r - nf * L;
                     }
-                    slot = (ti < 32 ? 0 : 32 * rows0) + it * 32 + (ti & 31);
+                    slot = (ti < 32 ? 0 : kP2GSlotPitch * rows0) + it * kP2GSlotPitch + (ti & 31);
                 }
                 const int p = pp[u];
                 int bc[3];
@@ -387,7 +394,8 @@ __global__ void __launch_bounds__(kP2GThreads, 4) k_p2g(StepArgs a)
 #pragma unroll
             for (int q = 0; q < 9; ++q) { acc_w[q] = 0.f; acc_p[q][0] = acc_p[q][1] = acc_p[q][2] = 0.f; }
             if (t < n_items)
-                item_accumulate<kP2GSlots>(rec, inter ? (t < 32 ? 0 : 32 * rows0) + (t & 31) : it_beg[t], inter ? 32 : 1,
+                item_accumulate<kP2GSlots>(rec, inter ? (t < 32 ? 0 : kP2GSlotPitch * rows0) + (t & 31) : it_beg[t],
+                                           inter ? kP2GSlotPitch : 1,
                                            it_len[t], slice, acc_w, acc_p);
             __syncthreads();
             if (t < n_items) {
