@@ -86,7 +86,8 @@ enum {
                                    1: one launch per phase per scene (looped)       */
     MPM_OPT_P2G_THREADS = 3,    /* threads per CTA of the P2G kernel: fixed at 192
                                    (64 cells x 3 node slices); other values rejected */
-    MPM_OPT_G2P_THREADS = 4,    /* threads per CTA of the G2P kernel: 128/256/512   */
+    MPM_OPT_G2P_THREADS = 4,    /* threads per CTA of the G2P kernel: 128 (default) /
+                                   256 / 512                                        */
     MPM_OPT_CTAS_PER_SM = 5,    /* persistent CTAs per SM for P2G/G2P (0 = occupancy max) */
     MPM_OPT_GRAPH_CHUNK = 6,    /* substeps captured per graph (1..64)              */
     MPM_OPT_PHASE_TIMING = 7,   /* 0/1: record CUDA events around each phase of every
@@ -169,6 +170,10 @@ const char* mpm_status_string(int status);
 /* Set a tuning/launch option (MPM_OPT_*).  INVALID_ARGUMENT for an unknown
  * option or an unsupported value. */
 int mpm_set_option(mpm_ctx* ctx, int option, int64_t value);
+
+/* Current value of a tuning/launch option (MPM_OPT_*), e.g. what mpm_autotune
+ * chose, into *value.  INVALID_ARGUMENT for an unknown option or NULL. */
+int mpm_get_option(mpm_ctx* ctx, int option, int64_t* value);
 
 /* ---- factory (Sec. V-B) ---------------------------------------------- */
 

@@ -383,6 +383,25 @@ extern "C" int mpm_destroy(mpm_ctx* c)
     return MPM_OK;
 }
 
+extern "C" int mpm_get_option(mpm_ctx* c, int option, int64_t* value)
+{
+    if (!c || !value) return MPM_ERR_INVALID_ARGUMENT;
+    switch (option) {
+    case MPM_OPT_USE_GRAPHS: *value = c->use_graphs; break;
+    case MPM_OPT_LAUNCH_MODE: *value = c->launch_mode; break;
+    case MPM_OPT_P2G_THREADS: *value = kP2GThreads; break;
+    case MPM_OPT_G2P_THREADS: *value = c->g2p_threads; break;
+    case MPM_OPT_CTAS_PER_SM: *value = c->ctas_per_sm; break;
+    case MPM_OPT_GRAPH_CHUNK: *value = c->graph_chunk; break;
+    case MPM_OPT_PHASE_TIMING: *value = c->phase_timing; break;
+    case MPM_OPT_P2G_CHUNK: *value = c->p2g_chunk; break;
+    case MPM_OPT_FUSED: *value = c->fused; break;
+    case MPM_OPT_G2P_REGS64: *value = c->g2p_regs64; break;
+    default: return MPM_ERR_INVALID_ARGUMENT;
+    }
+    return MPM_OK;
+}
+
 extern "C" int mpm_set_option(mpm_ctx* c, int option, int64_t value)
 {
     if (!c) return MPM_ERR_INVALID_ARGUMENT;

@@ -67,6 +67,7 @@ _SIGS = {
     "mpm_destroy": (ct.c_int, [_P]),
     "mpm_status_string": (ct.c_char_p, [ct.c_int]),
     "mpm_set_option": (ct.c_int, [_P, ct.c_int, ct.c_int64]),
+    "mpm_get_option": (ct.c_int, [_P, ct.c_int, ct.POINTER(ct.c_int64)]),
     "mpm_add_particles": (ct.c_int, [_P, ct.c_int, ct.c_int64, _P, _P, _P, _P, ct.c_float, ct.c_float, ct.c_float,
                                      ct.c_float, ct.c_int, ct.POINTER(ct.c_int64)]),
     "mpm_set_rigid": (ct.c_int, [_P, ct.c_int, ct.c_int, ct.POINTER(mpm_rigid)]),
@@ -124,6 +125,13 @@ def mpm_status_string(status):
 def mpm_set_option(h, option, value):
     opt = OPT[option] if isinstance(option, str) else int(option)
     return _check(lib().mpm_set_option(h, opt, int(value)), "mpm_set_option")
+
+
+def mpm_get_option(h, option):
+    opt = OPT[option] if isinstance(option, str) else int(option)
+    v = ct.c_int64()
+    _check(lib().mpm_get_option(h, opt, ct.byref(v)), "mpm_get_option")
+    return v.value
 
 
 def mpm_add_particles(h, scene, n, x, v, E, nu, E0, nu0, rho, V0, mem):
@@ -308,6 +316,9 @@ class Simulation:
 
     def set_option(self, name, value):
         mpm_set_option(self.h, name, value)
+
+    def get_option(self, name):
+        return mpm_get_option(self.h, name)
 
     # factory
     def add_particles(self, scene, x, v=None, E=None, nu=None, *, E0=0.0, nu0=0.0, rho=1.0, V0=1.0):

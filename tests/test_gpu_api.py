@@ -161,6 +161,12 @@ def test_invalid_arguments():
             sim.substep(-1.0, 1)
         with pytest.raises(mpm.MPMError):
             sim.set_option("p2g_threads", 100)
+        with pytest.raises(mpm.MPMError):
+            sim.set_option("p2g_chunk", 192)
+        sim.set_option("g2p_threads", 512)
+        assert sim.get_option("g2p_threads") == 512
+        with pytest.raises(mpm.MPMError):
+            sim.get_option(99)
         with pytest.raises(mpm.MPMError) as e:
             sim.backward()
         assert e.value.status in (-1, -9)
@@ -173,6 +179,10 @@ def test_autotune_restores_state():
         before = sim.read_state(0)
         ms = sim.autotune(sc["dt"], 3)
         assert ms > 0
+        # the chosen launch shape is one of the candidates
+        assert sim.get_option("p2g_chunk") in (384, 576, 768)
+        assert sim.get_option("g2p_threads") in (128, 256, 512)
+        assert sim.get_option("g2p_regs64") in (0, 1) and sim.get_option("ctas_per_sm") in (0, 2)
         after = sim.read_state(0)
         for f in ("x", "v", "C", "F"):
             assert np.array_equal(before[f], after[f])
