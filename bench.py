@@ -197,12 +197,22 @@ def recorded_traffic(kernel):
 
 
 def algorithmic_bytes(N, bricks, active_nodes, pp_mat=False):
-    extra = 8 if pp_mat else 0
+    """Bytes each phase must move at least once per substep (the table of the
+    kernels and their bounds):
+      sort  scan: brick count + node flag (8 B per brick of the grid); scatter:
+            key, rank and the brick offset read, slot written (16 B per particle)
+      p2g   perm 4 + x 12 + v 12 + C 36 + tau 24 read, perm 4 rewritten in cell
+            order (92 B per particle) + one 16-B reduction per active node
+      grid  (m, mv) read, (v, m) written, (m, mv) cleared: 48 B per active node
+      g2p   perm 4 + x 12 + F 36 + id 4 read; x, v, C, F 96 + tau 24 + id 4 +
+            key, rank 8 written (188 B per particle; + mu, lam 16 with
+            per-particle materials) + the velocity window, 16 B per active node"""
+    extra = 16 if pp_mat else 0
     return {
-        "sort": 4 * bricks + 16 * N,
-        "p2g": (100 + extra) * N + 16 * active_nodes,
+        "sort": 8 * bricks + 16 * N,
+        "p2g": 92 * N + 16 * active_nodes,
         "grid": 48 * active_nodes,
-        "g2p": (164 + 2 * extra) * N + 16 * active_nodes,
+        "g2p": (188 + extra) * N + 16 * active_nodes,
     }
 
 
@@ -338,6 +348,7 @@ def run_ours(args):
 
     if not args.no_extras and rank == 0:
         line["batched"] = run_batched(args, stream)
+        line["scale_sweep"] = run_scale_sweep(stream)
         line["cpu_baseline"] = run_cpu_baseline(sc)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -374,6 +385,42 @@ def run_batched(args, stream):
     out["speedup_vs_looped_direct"] = out["batched_graph"] / out["looped_direct"]
     out["speedup_vs_looped_graph"] = out["batched_graph"] / out["looped_graph"]
     return out
+
+
+def run_scale_sweep(stream):
+    """The scale-sweep tissue blocks (64k, 256k, 1M, 4M particles): particle-substeps/s
+    in graph replay over 100 substeps after 30 of warm-up, and per kernel the
+    algorithmic GB/s from phase events over 20 more substeps."""
+    import torch
+
+    from paper_2502_18437_gb300 import mpm, workloads
+
+    peak, _ = measured_peaks()
+    out = {}
+    for N in sorted(workloads.SCALE_POINTS):
+        sc = workloads.tissue_block(N=N)
+        n, dt = sc["n"], sc["dt"]
+        sim = mpm.from_workload(sc, stream=stream.cuda_stream)
+        sim.substep(dt, 30)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sim.substep(dt, 100)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 100
+        sim.set_option("phase_timing", 1)
+        sim.phase_stats(reset=True)
+        sim.substep(dt, 20)
+        ps = sim.phase_stats(reset=True)
+        sim.close()
+        ab = algorithmic_bytes(N, (n // 4) ** 3, ps["active_nbricks"] * 64)
+        per = {k: ps["ms"][i] / ps["substeps"] for i, k in enumerate(["sort", "p2g", "grid", "g2p"])}
+        out[str(N)] = {"grid": f"{n}^3", "value": N / (ms / 1e3), "ms_per_substep": round(ms, 5),
+                       "kernel_gbs": {k: round(ab[k] / (per[k] / 1e3) / 1e9, 1) for k in per},
+                       "kernel_frac": {k: round(ab[k] / (per[k] / 1e3) / 1e9 / peak, 3) for k in per},
+                       "active_pbricks": ps["active_pbricks"], "active_nbricks": ps["active_nbricks"]}
+    return {"unit": "particle-substeps/s", "points": out}
 
 
 def run_cpu_baseline(sc):
