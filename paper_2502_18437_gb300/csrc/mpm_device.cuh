@@ -224,6 +224,40 @@ __device__ __forceinline__ void svd3(const float F[9], float U[9], float s[3], f
     s[2] = B[8];
 }
 
+// Left stretch of F for the constitutive update: the eigen-decomposition
+// F F^T = U diag(l) U^T (cyclic Jacobi, 4 sweeps, U accumulated) and the signed
+// singular values of the rotation-variant SVD F = U diag(s) V^T (V a rotation).
+// The two larger are sqrt(l); the smallest is det F / (their product), signed
+// like det F and accurate where sqrt of a tiny eigenvalue of F F^T is not.  V is
+// never formed: the stress needs U and s only, and the plastic return map is
+// F' = U diag(s'/s) U^T F.
+__device__ __forceinline__ void left_stretch(const float F[9], float U[9], float s[3])
+{
+    float a00 = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
+    float a01 = F[0] * F[3] + F[1] * F[4] + F[2] * F[5];
+    float a02 = F[0] * F[6] + F[1] * F[7] + F[2] * F[8];
+    float a11 = F[3] * F[3] + F[4] * F[4] + F[5] * F[5];
+    float a12 = F[3] * F[6] + F[4] * F[7] + F[5] * F[8];
+    float a22 = F[6] * F[6] + F[7] * F[7] + F[8] * F[8];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) U[i] = (i % 4 == 0) ? 1.0f : 0.0f;
+#pragma unroll
+    for (int sweep = 0; sweep < 4; ++sweep) {
+        jacobi_rot(a00, a11, a01, a02, a12, U[0], U[1], U[3], U[4], U[6], U[7]);
+        jacobi_rot(a00, a22, a02, a01, a12, U[0], U[2], U[3], U[5], U[6], U[8]);
+        jacobi_rot(a11, a22, a12, a01, a02, U[1], U[2], U[4], U[5], U[7], U[8]);
+    }
+    const float J = det3(F);
+    const float r0 = approx_sqrt(a00), r1 = approx_sqrt(a11), r2 = approx_sqrt(a22);
+    // smallest eigenvalue: its singular value from the determinant
+    const int m = (a00 <= a11 && a00 <= a22) ? 0 : (a11 <= a22 ? 1 : 2);
+    const float pa = m == 0 ? r1 * r2 : (m == 1 ? r0 * r2 : r0 * r1);
+    const float sm = pa > 1e-30f ? __fdividef(J, pa) : 0.0f;
+    s[0] = m == 0 ? sm : r0;
+    s[1] = m == 1 ? sm : r1;
+    s[2] = m == 2 ? sm : r2;
+}
+
 // R = U V^T
 __device__ __forceinline__ void mul_abt(const float A[9], const float B[9], float out[9])
 {
@@ -255,10 +289,10 @@ __device__ __forceinline__ unsigned constitutive(int model, int plastic, float y
 {
     unsigned e = 0u;
     if (model == MPM_FIXED_COROTATED || plastic) {
-        float U[9], s[3], V[9];
-        svd3(F, U, s, V);
+        float U[9], s[3];
+        left_stretch(F, U, s);
         if (plastic) {
-            if (!(s[2] > 0.0f)) {
+            if (!(s[0] > 0.0f && s[1] > 0.0f && s[2] > 0.0f)) {
                 e |= MPM_EBIT_INVERTED;
             } else {
                 const float e0 = __logf(s[0]), e1 = __logf(s[1]), e2 = __logf(s[2]);
@@ -268,15 +302,29 @@ __device__ __forceinline__ unsigned constitutive(int model, int plastic, float y
                 const float gamma = nrm - __fdividef(yield, 2.0f * mu);
                 if (gamma > 0.0f && nrm > 0.0f) {
                     const float k = __fdividef(gamma, nrm);
-                    s[0] = __expf(e0 - k * d0);
-                    s[1] = __expf(e1 - k * d1);
-                    s[2] = __expf(e2 - k * d2);
+                    const float n0 = __expf(e0 - k * d0), n1 = __expf(e1 - k * d1), n2 = __expf(e2 - k * d2);
+                    // F' = U diag(s'/s) U^T F = U diag(s') V^T
+                    const float q0 = __fdividef(n0, s[0]), q1 = __fdividef(n1, s[1]), q2 = __fdividef(n2, s[2]);
+                    float M[9];
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+#pragma unroll
+                        for (int c = r; c < 3; ++c) {
+                            M[3 * r + c] = U[3 * r] * q0 * U[3 * c] + U[3 * r + 1] * q1 * U[3 * c + 1] +
+                                           U[3 * r + 2] * q2 * U[3 * c + 2];
+                            M[3 * c + r] = M[3 * r + c];
+                        }
+                    float Fp[9];
 #pragma unroll
                     for (int r = 0; r < 3; ++r)
 #pragma unroll
                         for (int c = 0; c < 3; ++c)
-                            F[3 * r + c] = U[3 * r] * s[0] * V[3 * c] + U[3 * r + 1] * s[1] * V[3 * c + 1] +
-                                           U[3 * r + 2] * s[2] * V[3 * c + 2];
+                            Fp[3 * r + c] = M[3 * r] * F[c] + M[3 * r + 1] * F[3 + c] + M[3 * r + 2] * F[6 + c];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) F[i] = Fp[i];
+                    s[0] = n0;
+                    s[1] = n1;
+                    s[2] = n2;
                 }
             }
         }
