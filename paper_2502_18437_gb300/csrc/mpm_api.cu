@@ -169,6 +169,9 @@ StepArgs step_args(mpm_ctx* c, float dt, int s0, int s1, const PState& in, const
     a.p2g_chunk = c->p2g_chunk;
     a.g2p_threads = c->g2p_threads;
     a.cell_order = 1;
+    a.any_rigid = 0;
+    for (int sc = s0; sc < s1; ++sc)
+        if (c->h_scenes[sc].n_rigid > 0) a.any_rigid = 1;
     return a;
 }
 
@@ -588,6 +591,7 @@ extern "C" int mpm_set_rigid(mpm_ctx* c, int scene, int rigid_id, const mpm_rigi
     if (c->h_scenes[scene].n_rigid != nr) {
         c->h_scenes[scene].n_rigid = nr;
         c->scenes_dirty = true;
+        clear_graphs(c);  // captured substeps carry whether any scene has a rigid
     }
     MPM_CK(cudaMemcpyAsync(c->d_rigids + slot, &c->h_rigids[slot], sizeof(RigidDev), cudaMemcpyHostToDevice, c->stream));
     int st = upload_scenes(c);

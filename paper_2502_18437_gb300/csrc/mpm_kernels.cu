@@ -696,59 +696,95 @@ __device__ __forceinline__ void grid_node(const StepArgs& a, int B, int scene, i
     }
 }
 
-__global__ void __launch_bounds__(kGridThreads) k_grid(StepArgs a)
+__global__ void __launch_bounds__(kGridThreads, 4) k_grid(StepArgs a)
 {
     __shared__ RigidCur rig[kMaxRigids];
     __shared__ float simp[kMaxRigids * 6];
+    // per brick of a chunk of the list: node brick, scene, the scene's rigid count
+    __shared__ int s_brk[kGridThreads], s_scn[kGridThreads], s_nr[kGridThreads];
     __shared__ int s_scene[4];
     __shared__ int s_staged, s_nrig, s_target;
     const int tid = threadIdx.x, lane = tid & 31, grp = tid >> 6, nid = tid & 63;
     const int n_nact = a.sb.counters[CTR_N_NACT];
-    if (tid == 0) { s_staged = -1; s_nrig = 0; }
-    for (int base = blockIdx.x * 4; base < n_nact; base += gridDim.x * 4) {
-        const int item = base + grp;
-        const int my_scene = item < n_nact ? a.sb.nact_scene[item] : -1;
-        const int my_nr = my_scene >= 0 ? a.scenes[my_scene].n_rigid : 0;
-        if (!__syncthreads_or(my_nr > 0)) {
-            // no rigid in any of the 4 bricks: no staging, no barriers
-            if (my_scene >= 0) grid_node(a, a.sb.nact_brick[item], my_scene, nid, lane, nullptr, 0, nullptr);
-            continue;
+    if (!a.any_rigid) {
+        // no scene has a rigid: 4 node bricks per step, no staging, no barriers
+        for (int base = blockIdx.x * 4; base < n_nact; base += gridDim.x * 4) {
+            const int item = base + grp;
+            if (item < n_nact) grid_node(a, a.sb.nact_brick[item], a.sb.nact_scene[item], nid, lane, nullptr, 0, nullptr);
         }
-        if (nid == 0) s_scene[grp] = my_scene;
-        bool done = my_scene < 0;
+        return;
+    }
+    if (tid == 0) { s_staged = -1; s_nrig = 0; }
+    // each CTA takes a contiguous run of the node-brick list (scenes are contiguous
+    // in it), so that it stages a scene's rigids and flushes their impulses about
+    // once; groups of 4 bricks of the staged scene (or of scenes without rigids)
+    // then run without barriers
+    const int per = ((n_nact + gridDim.x - 1) / gridDim.x + 3) & ~3;
+    const int first = blockIdx.x * per, last = min(first + per, n_nact);
+    for (int c0 = first; c0 < last; c0 += kGridThreads) {
+        const int c1 = min(c0 + kGridThreads, last);
+        __syncthreads();  // the previous chunk's table is no longer read
+        if (c0 + tid < c1) {
+            const int sc = a.sb.nact_scene[c0 + tid];
+            s_brk[tid] = a.sb.nact_brick[c0 + tid];
+            s_scn[tid] = sc;
+            s_nr[tid] = a.scenes[sc].n_rigid;
+        }
         __syncthreads();
-        for (;;) {
-            // next scene to process among the 4 bricks (usually all the same)
-            if (tid == 0) {
-                int t = -1;
-                for (int g = 0; g < 4; ++g)
-                    if (s_scene[g] >= 0 && (t < 0 || s_scene[g] < t)) t = s_scene[g];
-                s_target = t;
+        for (int base = c0; base < c1; base += 4) {
+            const int item = base + grp;
+            const int my_scene = item < c1 ? s_scn[item - c0] : -1;
+            const int gl = min(base + 3, c1 - 1) - c0;
+            bool no_rigid = true, staged = true;
+            for (int g = base - c0; g <= gl; ++g) {
+                no_rigid = no_rigid && s_nr[g] == 0;
+                staged = staged && s_scn[g] == s_staged;
             }
+            const int my_brick = my_scene >= 0 ? s_brk[item - c0] : 0;
+            if (no_rigid) {
+                if (my_scene >= 0) grid_node(a, my_brick, my_scene, nid, lane, nullptr, 0, nullptr);
+                continue;
+            }
+            if (staged) {
+                if (my_scene >= 0) grid_node(a, my_brick, my_scene, nid, lane, rig, s_nrig, simp);
+                continue;
+            }
+            if (nid == 0) s_scene[grp] = my_scene;
+            bool done = my_scene < 0;
             __syncthreads();
-            const int target = s_target;
-            if (target < 0) break;
-            if (target != s_staged) {
-                if (s_staged >= 0) flush_impulse(a, simp, s_staged, s_nrig, tid);
-                __syncthreads();
-                const int nr = a.scenes[target].n_rigid;
-                const double t_now = a.t_scene[target];
-                if (tid < nr) stage_rigid(a.rigids[target * kMaxRigids + tid], t_now, rig[tid]);
-                for (int t = tid; t < nr * kMaxPts * 3; t += kGridThreads) {
-                    const int r = t / (kMaxPts * 3), k = t % (kMaxPts * 3);
-                    rig[r].pts[k] = a.rigids[target * kMaxRigids + r].pts[k];
+            for (;;) {
+                // next scene to process among the 4 bricks (usually all the same)
+                if (tid == 0) {
+                    int t = -1;
+                    for (int g = 0; g < 4; ++g)
+                        if (s_scene[g] >= 0 && (t < 0 || s_scene[g] < t)) t = s_scene[g];
+                    s_target = t;
                 }
-                for (int t = tid; t < kMaxRigids * 6; t += kGridThreads) simp[t] = 0.f;
-                if (tid == 0) { s_staged = target; s_nrig = nr; }
+                __syncthreads();
+                const int target = s_target;
+                if (target < 0) break;
+                if (target != s_staged) {
+                    if (s_staged >= 0) flush_impulse(a, simp, s_staged, s_nrig, tid);
+                    __syncthreads();
+                    const int nr = a.scenes[target].n_rigid;
+                    const double t_now = a.t_scene[target];
+                    if (tid < nr) stage_rigid(a.rigids[target * kMaxRigids + tid], t_now, rig[tid]);
+                    for (int t = tid; t < nr * kMaxPts * 3; t += kGridThreads) {
+                        const int r = t / (kMaxPts * 3), k = t % (kMaxPts * 3);
+                        rig[r].pts[k] = a.rigids[target * kMaxRigids + r].pts[k];
+                    }
+                    for (int t = tid; t < kMaxRigids * 6; t += kGridThreads) simp[t] = 0.f;
+                    if (tid == 0) { s_staged = target; s_nrig = nr; }
+                    __syncthreads();
+                }
+                if (!done && my_scene == target) {
+                    done = true;
+                    grid_node(a, my_brick, target, nid, lane, rig, s_nrig, simp);
+                }
+                __syncthreads();
+                if (nid == 0 && my_scene == target) s_scene[grp] = -1;
                 __syncthreads();
             }
-            if (!done && my_scene == target) {
-                done = true;
-                grid_node(a, a.sb.nact_brick[item], target, nid, lane, rig, s_nrig, simp);
-            }
-            __syncthreads();
-            if (nid == 0 && my_scene == target) s_scene[grp] = -1;
-            __syncthreads();
         }
     }
     __syncthreads();

@@ -55,6 +55,7 @@ struct StepArgs {
     int fused_ctas;              // CTAs of the fused G2P + P2G kernel
     int p2g_chunk, g2p_threads, g2p_regs64;
     int tau_valid;               // P2G reads the stored stress (else recomputes it from F)
+    int any_rigid;               // some scene of the range has a rigid (contact in the grid update)
     int cell_order;              // P2G rewrites each pass's permutation slots in cell order
 };
 
