@@ -175,8 +175,8 @@ StepArgs step_args(mpm_ctx* c, float dt, int s0, int s1, const PState& in, const
     return a;
 }
 
-// One substep of every scene.  Unfused: sort, P2G, grid update, G2P.  Fused
-// (default): sort, P2G only when G does not already hold this state's P2G
+// One substep of every scene.  Unfused (default): sort, P2G, grid update, G2P.
+// Fused (MPM_OPT_FUSED): sort, P2G only when G does not already hold this state's P2G
 // (need_p2g), grid update, then the fused G2P + P2G, which leaves the next
 // substep's P2G in G.
 int enqueue_substep(mpm_ctx* c, float dt, const PState& in, const PState& out, bool need_p2g)

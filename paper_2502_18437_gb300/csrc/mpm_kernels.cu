@@ -3,8 +3,9 @@
 //   k_scan     brick histogram -> particle offsets, active particle-brick and
 //              node-brick lists (single-pass decoupled look-back scan)
 //   k_scatter  counting-sort scatter: permutation sorted slot -> particle
-//   k_p2g      P2G (Eq. 1, Eq. 8) into a shared-memory 6^3 node window per
-//              brick, flushed to HBM with vector atomics
+//   k_p2g      P2G (Eq. 1, Eq. 8): balanced per-cell work items summed in
+//              registers into shared-memory 6^3 node windows per brick, flushed
+//              to HBM with vector atomics; leaves the permutation in cell order
 //   k_grid     grid update (Eq. 3), rigid contact (Sec. IV, Eq. 11, Eq. 12),
 //              domain walls, reset of the P2G accumulator
 //   k_g2p      G2P (Eq. 4, Eq. 9, Eq. 10) with the 2x2x2-brick velocity halo
@@ -17,11 +18,13 @@ namespace mpm {
 
 // ----------------------------------------------------------------- scan
 //
-// One tile = 2048 consecutive bricks of the range.  Each brick contributes
-// (particles, is an active particle brick, is an active node brick); a node
-// brick is active when it or one of its 7 lower neighbours (-1 in any subset
-// of the axes) holds particles, since a particle's 3-node stencil reaches at
-// most 2 nodes beyond its base cell, i.e. into the next brick.
+// One tile = kScanTile (1024) consecutive bricks of the range.  Each brick
+// contributes (particles, is an active particle brick, is an active node brick);
+// a node brick is active when it or one of its 7 lower neighbours (-1 in any
+// subset of the axes) holds particles, since a particle's 3-node stencil reaches
+// at most 2 nodes beyond its base cell, i.e. into the next brick.  The key
+// producers (G2P, k_prepare) flag those bricks when the first particles enter a
+// brick, so the scan reads one count and one flag per brick and clears the flag.
 
 __device__ __forceinline__ int4 add4(int4 a, int4 b) { return make_int4(a.x + b.x, a.y + b.y, a.z + b.z, 0); }
 

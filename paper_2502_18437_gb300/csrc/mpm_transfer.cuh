@@ -1,6 +1,7 @@
 // Device helpers shared by the forward and adjoint transfer kernels: PTX
 // wrappers (mbarrier, bulk-copy TMA, vector reductions), brick keys and ranks,
-// B-spline weights, P2G coefficients, per-cell accumulation, halo staging.
+// B-spline weights, P2G coefficients, the P2G item schedule and accumulation,
+// halo staging.
 #pragma once
 
 #include "mpm_kernels.cuh"
