@@ -262,7 +262,7 @@ static void free_ctx(mpm_ctx* c)
     mpm_tape_free(c);
     clear_graphs(c);
     for (int i = 0; i < 2; ++i) cudaFree(c->state_mem[i]);
-    void* bufs[] = {c->sb.key, c->sb.rank, c->sb.perm, c->sb.cnt, c->sb.nflag, c->sb.off, c->sb.act_brick, c->sb.act_start,
+    void* bufs[] = {c->sb.key, c->sb.rank, c->sb.perm, c->sb.scell, c->sb.cnt, c->sb.nflag, c->sb.off, c->sb.act_brick, c->sb.act_start,
                     c->sb.act_count, c->sb.act_scene, c->sb.nact_brick, c->sb.nact_scene, c->sb.counters,
                     c->sb.tile_status, c->sb.tile_agg, c->sb.tile_incl, c->G, c->V, c->brick_epoch,
                     c->d_scenes, c->d_rigids, c->d_impulse, c->d_err, c->d_time, c->d_epoch, c->d_stage};
@@ -332,6 +332,7 @@ extern "C" int mpm_create(const mpm_config* cfg, void* stream, mpm_ctx** out)
     alloc((void**)&c->sb.key, sizeof(int) * c->cap);
     alloc((void**)&c->sb.rank, sizeof(int) * c->cap);
     alloc((void**)&c->sb.perm, sizeof(int) * c->cap);
+    alloc((void**)&c->sb.scell, c->cap);
     alloc((void**)&c->sb.cnt, sizeof(int) * nbk);
     alloc((void**)&c->sb.nflag, sizeof(int) * nbk);
     alloc((void**)&c->sb.off, sizeof(int) * nbk);

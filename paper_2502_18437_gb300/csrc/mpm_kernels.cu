@@ -204,10 +204,14 @@ __global__ void k_scatter(StepArgs a, int n_tiles, int write_perm)
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = a.r.p0 + g;
     if (write_perm && g < a.r.np) {
-        const int key = a.sb.key[i];
-        const int dst = (key >= a.r.bb0 && key < a.r.bb0 + a.r.nbr) ? __ldg(&a.sb.off[key]) + a.sb.rank[i] : -1;
-        if (dst >= a.r.p0 && dst < a.r.p0 + a.r.np) a.sb.perm[dst] = i;
-        else atomicOr(&a.err[a.r.s0], MPM_EBIT_INTERNAL);
+        const int key = a.sb.key[i], brick = key >> 6;
+        const int dst = (brick >= a.r.bb0 && brick < a.r.bb0 + a.r.nbr) ? __ldg(&a.sb.off[brick]) + a.sb.rank[i] : -1;
+        if (dst >= a.r.p0 && dst < a.r.p0 + a.r.np) {
+            a.sb.perm[dst] = i;
+            a.sb.scell[dst] = (unsigned char)(key & 63);
+        } else {
+            atomicOr(&a.err[a.r.s0], MPM_EBIT_INTERNAL);
+        }
     }
     if (g < n_tiles) a.sb.tile_status[g] = 0u;
     if (g == 0) a.sb.counters[CTR_TICKET] = 0;
@@ -234,10 +238,10 @@ __global__ void k_prepare(StepArgs a, PState st)
     const SceneDev sc = a.scenes[scene];
     if (valid) {
         unsigned ood = 0;
-        key = brick_key(sc, st.x[i], st.x[a.cap + i], st.x[2 * a.cap + i], ood);
+        key = cell_key(sc, st.x[i], st.x[a.cap + i], st.x[2 * a.cap + i], ood);
         if (ood) ebits |= MPM_EBIT_OUT_OF_DOMAIN;
     }
-    const int rank = aggregated_rank_mark(a.sb.cnt, a.sb.nflag, sc, key, valid);
+    const int rank = aggregated_rank_mark(a.sb.cnt, a.sb.nflag, sc, key >> 6, valid);
     if (valid) {
         a.sb.key[i] = key;
         a.sb.rank[i] = rank;
@@ -249,7 +253,8 @@ __global__ void k_prepare(StepArgs a, PState st)
 //
 // One CTA per active particle brick (4^3 cells, a 6^3-node window), 192
 // threads.  Per pass over up to PER x 192 particles of the brick:
-//   A1. one thread per particle: base cell and rank inside the cell;
+//   A1. one thread per particle: base cell (stored by the sort beside the
+//      permutation) and rank inside the cell;
 //   (warp 0) the cells' particles are cut into at most 64 balanced work items
 //      (build_items), so that the lanes of a warp run loops of nearly equal
 //      length instead of as long as the warp's fullest cell;
@@ -314,7 +319,6 @@ __global__ void __launch_bounds__(kP2GThreads, 4) k_p2g(StepArgs a)
             const int cn = min(CHUNK, count - c0);
             // A1: cell and rank of each particle of the pass
             int pp[PER], pc[PER], pr[PER];
-            float px[PER][3];
 #pragma unroll
             for (int u = 0; u < PER; ++u) {
                 const int k = tid + u * kP2GThreads;
@@ -322,16 +326,19 @@ __global__ void __launch_bounds__(kP2GThreads, 4) k_p2g(StepArgs a)
                 if (k < cn) {
                     const int p = a.sb.perm[start + c0 + k];
                     pp[u] = p;
-                    px[u][0] = a.in.x[p];
-                    px[u][1] = a.in.x[cap + p];
-                    px[u][2] = a.in.x[2 * cap + p];
-                    int c[3];
-                    const unsigned ood = base_cell(px[u][0], n, c[0]) | base_cell(px[u][1], n, c[1]) |
-                                         base_cell(px[u][2], n, c[2]);
-                    if (ood) ebits |= MPM_EBIT_OUT_OF_DOMAIN;
-                    const int l0 = min(max(c[0] - ox, 0), 3), l1 = min(max(c[1] - oy, 0), 3),
-                              l2 = min(max(c[2] - oz, 0), 3);
-                    pc[u] = (l0 * 4 + l1) * 4 + l2;
+                    if (a.cell_order) {
+                        // the sort stored each slot's cell: no dependent load of x here
+                        pc[u] = a.sb.scell[start + c0 + k];
+                    } else {
+                        // a recorded permutation (differentiation): the cell from x
+                        int c[3];
+                        const unsigned ood = base_cell(a.in.x[p], n, c[0]) | base_cell(a.in.x[cap + p], n, c[1]) |
+                                             base_cell(a.in.x[2 * cap + p], n, c[2]);
+                        if (ood) ebits |= MPM_EBIT_OUT_OF_DOMAIN;
+                        const int l0 = min(max(c[0] - ox, 0), 3), l1 = min(max(c[1] - oy, 0), 3),
+                                  l2 = min(max(c[2] - oz, 0), 3);
+                        pc[u] = (l0 * 4 + l1) * 4 + l2;
+                    }
                     pr[u] = atomicAdd(&cell_cnt[pc[u]], 1);
                 }
             }
@@ -370,7 +377,7 @@ __global__ void __launch_bounds__(kP2GThreads, 4) k_p2g(StepArgs a)
                 const int p = pp[u];
                 int bc[3];
                 float f[3], w[9];
-                particle_weights(px[u][0], px[u][1], px[u][2], n, bc, f, w);
+                ebits |= particle_weights(a.in.x[p], a.in.x[cap + p], a.in.x[2 * cap + p], n, bc, f, w);
                 float C[9], v[3], t6[6];
 #pragma unroll
                 for (int q = 0; q < 9; ++q) C[q] = a.in.C[(size_t)q * cap + p];
@@ -955,10 +962,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_g2p(StepArgs a)
 #pragma unroll
                 for (int q = 0; q < 6; ++q) a.out.tau[(size_t)q * a.cap + start + k] = o.t6[q];
                 unsigned ood = 0;
-                key = brick_key(sc, o.x[0], o.x[1], o.x[2], ood);
+                key = cell_key(sc, o.x[0], o.x[1], o.x[2], ood);
                 if (ood && !(ebits & MPM_EBIT_NONFINITE)) ebits |= MPM_EBIT_OUT_OF_DOMAIN;
             }
-            const int rank = aggregated_rank_mark(a.sb.cnt, a.sb.nflag, sc, key, valid);
+            const int rank = aggregated_rank_mark(a.sb.cnt, a.sb.nflag, sc, key >> 6, valid);
             if (valid) {
                 a.sb.key[start + k] = key;
                 a.sb.rank[start + k] = rank;
@@ -1029,7 +1036,8 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_g2p2g(StepArgs a)
                 float f[3], w[9];
                 const unsigned ood = particle_weights(o.x[0], o.x[1], o.x[2], n, bc, f, w);
                 if (ood && !(ebits & MPM_EBIT_NONFINITE)) ebits |= ood;
-                key = sc.brick_base + ((bc[0] >> 2) * nb + (bc[1] >> 2)) * nb + (bc[2] >> 2);
+                key = (sc.brick_base + ((bc[0] >> 2) * nb + (bc[1] >> 2)) * nb + (bc[2] >> 2)) * 64 +
+                      ((bc[0] & 3) * 16 + (bc[1] & 3) * 4 + (bc[2] & 3));
                 float q3[3], Ad[9];
                 p2g_coeffs(m, kA, dxs, o.v, o.C, o.t6, f, q3, Ad);
                 const int l0 = bc[0] - ox, l1 = bc[1] - oy, l2 = bc[2] - oz;
@@ -1068,7 +1076,7 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_g2p2g(StepArgs a)
                             }
                 }
             }
-            const int rank = aggregated_rank_mark(a.sb.cnt, a.sb.nflag, sc, key, valid);
+            const int rank = aggregated_rank_mark(a.sb.cnt, a.sb.nflag, sc, key >> 6, valid);
             if (valid) {
                 a.sb.key[start + k] = key;
                 a.sb.rank[start + k] = rank;

@@ -12,9 +12,10 @@ struct Range {
 };
 
 struct SortBufs {
-    int* key;       // [cap] brick of each stored particle (next substep)
+    int* key;       // [cap] brick x 64 + base cell of each stored particle (next substep)
     int* rank;      // [cap] rank of the particle within its brick
     int* perm;      // [cap] sorted slot -> storage index
+    unsigned char* scell; // [cap] sorted slot -> base cell inside its brick (the key's low 6 bits)
     int* cnt;       // [bricks] particles per brick (next substep)
     int* nflag;     // [bricks] node brick touched by a particle brick's stencil (set by the
                     // key producers, consumed and cleared by the scan)

@@ -86,11 +86,14 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // ----------------------------------------------------- brick key + rank
 
-__device__ __forceinline__ int brick_key(const SceneDev& sc, float x0, float x1, float x2, unsigned& ood)
+// Sort key of a particle: its brick (global index) x 64 + its base cell inside
+// the brick.  The sort orders by brick (key >> 6); P2G reads the cell back.
+__device__ __forceinline__ int cell_key(const SceneDev& sc, float x0, float x1, float x2, unsigned& ood)
 {
     int c0, c1, c2;
     ood |= (unsigned)(base_cell(x0, sc.n, c0) | base_cell(x1, sc.n, c1) | base_cell(x2, sc.n, c2));
-    return sc.brick_base + ((c0 >> 2) * sc.nb + (c1 >> 2)) * sc.nb + (c2 >> 2);
+    const int brick = sc.brick_base + ((c0 >> 2) * sc.nb + (c1 >> 2)) * sc.nb + (c2 >> 2);
+    return brick * 64 + ((c0 & 3) * 16 + (c1 & 3) * 4 + (c2 & 3));
 }
 
 // Warp-aggregated rank: lanes with the same key get consecutive ranks from one
