@@ -649,7 +649,7 @@ int mpm_tape_record_substep(mpm_ctx* c, float dt)
 // counts from the positions, then the scan (lists, offsets) without a scatter.
 static int sort_with_perm(mpm_ctx* c, StepArgs& a, const PState& state, int* perm)
 {
-    MPM_CKA(cudaMemsetAsync(c->sb.cnt, 0, sizeof(int) * (size_t)c->total_bricks, c->stream));
+    MPM_CKA(reset_histogram(c));
     MPM_CKA(launch_prepare(a, state, c->stream));
     MPM_CKA(launch_sort(a, c->stream, false));
     a.sb.perm = perm;

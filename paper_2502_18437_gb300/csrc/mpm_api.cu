@@ -130,6 +130,8 @@ StepArgs step_args(mpm_ctx* c, float dt, int s0, int s1, const PState& in, const
     a.r.s1 = s1;
     a.r.bb0 = c->brick_base[s0];
     a.r.nbr = c->brick_base[s1] - c->brick_base[s0];
+    a.r.t0 = c->tile_base[s0];
+    a.r.nt = c->tile_base[s1] - c->tile_base[s0];
     a.r.p0 = c->h_scenes[s0].p_begin;
     int pend = s1 < c->n_scenes ? c->h_scenes[s1].p_begin : c->total_particles;
     a.r.np = pend - a.r.p0;
@@ -223,10 +225,19 @@ int invalidate_pending(mpm_ctx* c)
     return MPM_OK;
 }
 
+cudaError_t reset_histogram(mpm_ctx* c)
+{
+    const size_t nbk = (size_t)c->total_bricks;
+    cudaError_t e = cudaMemsetAsync(c->sb.cnt, 0, sizeof(int) * nbk, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->sb.nflag, 0, sizeof(int) * nbk, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->sb.tile_sum, 0, sizeof(int4) * (size_t)c->total_tiles, c->stream);
+    return e;
+}
+
 int ensure_keys(mpm_ctx* c)
 {
     if (c->keys_valid) return MPM_OK;
-    MPM_CK(cudaMemsetAsync(c->sb.cnt, 0, sizeof(int) * (size_t)c->total_bricks, c->stream));
+    MPM_CK(reset_histogram(c));
     StepArgs a = step_args(c, 0.f, 0, c->n_scenes, c->st[c->cur], c->st[c->cur ^ 1]);
     MPM_CK(launch_prepare(a, c->st[c->cur], c->stream));
     c->keys_valid = true;
@@ -264,7 +275,7 @@ static void free_ctx(mpm_ctx* c)
     for (int i = 0; i < 2; ++i) cudaFree(c->state_mem[i]);
     void* bufs[] = {c->sb.key, c->sb.rank, c->sb.perm, c->sb.scell, c->sb.cnt, c->sb.nflag, c->sb.off, c->sb.act_brick, c->sb.act_start,
                     c->sb.act_count, c->sb.act_scene, c->sb.nact_brick, c->sb.nact_scene, c->sb.counters,
-                    c->sb.tile_status, c->sb.tile_agg, c->sb.tile_incl, c->G, c->V, c->brick_epoch,
+                    c->sb.tile_sum, c->G, c->V, c->brick_epoch,
                     c->d_scenes, c->d_rigids, c->d_impulse, c->d_err, c->d_time, c->d_epoch, c->d_stage};
     for (void* p : bufs) cudaFree(p);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -302,6 +313,27 @@ extern "C" int mpm_create(const mpm_config* cfg, void* stream, mpm_ctx** out)
     if (bricks * 64 >= ((long long)1 << 31)) { delete c; return MPM_ERR_INVALID_ARGUMENT; }
     c->brick_base[c->n_scenes] = (int)bricks;
     c->total_bricks = (int)bricks;
+    // scan tiles: 2^shift bricks of one scene, at least 1024; wider tiles keep
+    // the number of tiles (whose totals every scan CTA adds up) near 2048 or less
+    {
+        int shift = 10;
+        auto tiles = [&](int sh) {
+            long long t = 0;
+            for (int s = 0; s < c->n_scenes; ++s)
+                t += ((long long)(c->brick_base[s + 1] - c->brick_base[s]) + (1 << sh) - 1) >> sh;
+            return t;
+        };
+        while (shift < 24 && tiles(shift) > 2048) ++shift;
+        c->sb.tile_shift = shift;
+        c->tile_base.resize(c->n_scenes + 1);
+        int t = 0;
+        for (int s = 0; s < c->n_scenes; ++s) {
+            c->tile_base[s] = t;
+            t += (c->brick_base[s + 1] - c->brick_base[s] + (1 << shift) - 1) >> shift;
+        }
+        c->tile_base[c->n_scenes] = t;
+        c->total_tiles = t;
+    }
     c->cap = (int)std::max<int64_t>(cfg->max_particles, 1);
     c->h_scenes.resize(c->n_scenes);
     for (int s = 0; s < c->n_scenes; ++s) {
@@ -310,6 +342,7 @@ extern "C" int mpm_create(const mpm_config* cfg, void* stream, mpm_ctx** out)
         d.n = c->scene_n[s];
         d.nb = d.n / 4;
         d.brick_base = c->brick_base[s];
+        d.tile_base = c->tile_base[s];
     }
     c->h_rigids.assign((size_t)c->n_scenes * kMaxRigids, RigidDev{});
     c->rigid_type.assign((size_t)c->n_scenes * kMaxRigids, MPM_RIGID_NONE);
@@ -324,7 +357,6 @@ extern "C" int mpm_create(const mpm_config* cfg, void* stream, mpm_ctx** out)
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e == cudaSuccess) e = prepare_p2g();
     const size_t nbk = (size_t)c->total_bricks;
-    c->n_tiles_max = (int)((nbk + kScanTile - 1) / kScanTile);
     auto alloc = [&](void** p, size_t bytes) {
         if (e == cudaSuccess) e = cudaMalloc(p, bytes ? bytes : 16);
     };
@@ -343,9 +375,7 @@ extern "C" int mpm_create(const mpm_config* cfg, void* stream, mpm_ctx** out)
     alloc((void**)&c->sb.nact_brick, sizeof(int) * nbk);
     alloc((void**)&c->sb.nact_scene, sizeof(int) * nbk);
     alloc((void**)&c->sb.counters, sizeof(int) * CTR_COUNT);
-    alloc((void**)&c->sb.tile_status, sizeof(unsigned) * c->n_tiles_max);
-    alloc((void**)&c->sb.tile_agg, sizeof(int4) * c->n_tiles_max);
-    alloc((void**)&c->sb.tile_incl, sizeof(int4) * c->n_tiles_max);
+    alloc((void**)&c->sb.tile_sum, sizeof(int4) * c->total_tiles);
     alloc((void**)&c->G, sizeof(float4) * nbk * 64);
     alloc((void**)&c->V, sizeof(float4) * nbk * 64);
     alloc((void**)&c->brick_epoch, sizeof(int) * nbk);
@@ -361,7 +391,7 @@ extern "C" int mpm_create(const mpm_config* cfg, void* stream, mpm_ctx** out)
         cudaMemsetAsync(c->sb.cnt, 0, sizeof(int) * nbk, c->stream);
         cudaMemsetAsync(c->sb.nflag, 0, sizeof(int) * nbk, c->stream);
         cudaMemsetAsync(c->sb.counters, 0, sizeof(int) * CTR_COUNT, c->stream);
-        cudaMemsetAsync(c->sb.tile_status, 0, sizeof(unsigned) * c->n_tiles_max, c->stream);
+        cudaMemsetAsync(c->sb.tile_sum, 0, sizeof(int4) * c->total_tiles, c->stream);
         cudaMemsetAsync(c->G, 0, sizeof(float4) * nbk * 64, c->stream);
         cudaMemsetAsync(c->V, 0, sizeof(float4) * nbk * 64, c->stream);
         cudaMemsetAsync(c->brick_epoch, 0xff, sizeof(int) * nbk, c->stream);
@@ -823,7 +853,7 @@ extern "C" int mpm_autotune(mpm_ctx* c, float dt, int trial_substeps, float* bes
     // snapshot everything a substep changes
     const size_t sbytes = state_bytes(c->cap);
     const size_t nbk = (size_t)c->total_bricks;
-    const size_t total = sbytes + 2 * sizeof(int) * c->cap + sizeof(int) * nbk * 3 +
+    const size_t total = sbytes + 2 * sizeof(int) * c->cap + sizeof(int) * nbk * 3 + sizeof(int4) * c->total_tiles +
                          (sizeof(double) + sizeof(int) + sizeof(unsigned) + sizeof(double) * kMaxRigids * 6) * c->n_scenes;
     char* snap = nullptr;
     MPM_CK(cudaMalloc(&snap, total));
@@ -831,6 +861,7 @@ extern "C" int mpm_autotune(mpm_ctx* c, float dt, int trial_substeps, float* bes
     const int cur0 = c->cur;
     Item items[] = {{c->state_mem[cur0], sbytes}, {c->sb.key, sizeof(int) * c->cap}, {c->sb.rank, sizeof(int) * c->cap},
                     {c->sb.cnt, sizeof(int) * nbk}, {c->sb.nflag, sizeof(int) * nbk},
+                    {c->sb.tile_sum, sizeof(int4) * c->total_tiles},
                     {c->brick_epoch, sizeof(int) * nbk},
                     {c->d_time, sizeof(double) * c->n_scenes}, {c->d_epoch, sizeof(int) * c->n_scenes},
                     {c->d_err, sizeof(unsigned) * c->n_scenes},

@@ -29,7 +29,8 @@ struct mpm_ctx {
     mpm::PState st[2]{};
     int cur = 0;
     mpm::SortBufs sb{};
-    int n_tiles_max = 0;
+    std::vector<int> tile_base;  // first scan tile of each scene; n_scenes + 1 entries
+    int total_tiles = 0;
     float4* G = nullptr;
     float4* V = nullptr;
     int* brick_epoch = nullptr;
@@ -85,6 +86,9 @@ StepArgs step_args(mpm_ctx* c, float dt, int s0, int s1, const PState& in, const
 int enqueue_substep(mpm_ctx* c, float dt, const PState& in, const PState& out, bool need_p2g);
 int invalidate_pending(mpm_ctx* c);
 int ensure_keys(mpm_ctx* c);
+// Zero the brick histogram, the node-brick flags and the tile sums (before keys
+// are recomputed from stored positions).
+cudaError_t reset_histogram(mpm_ctx* c);
 int upload_scenes(mpm_ctx* c);
 int ensure_stage(mpm_ctx* c, size_t bytes);
 PState state_view(float* base, int cap);

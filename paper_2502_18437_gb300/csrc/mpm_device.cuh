@@ -34,7 +34,7 @@ struct SceneDev {
     int p_count;     // number of particles
     int pp_mat;      // 1: per-particle mu/lam arrays
     int n_rigid;     // rigid slots in use
-    int pad_;
+    int tile_base;   // first scan tile of the scene (tiles never straddle scenes)
     float m_p, V0;   // particle mass and initial volume
     float mu, lam;   // uniform Lame parameters (pp_mat == 0)
 };
@@ -74,7 +74,7 @@ struct PState {
 enum {
     CTR_N_ACT = 0,     // active particle bricks
     CTR_N_NACT = 1,    // active node bricks
-    CTR_TICKET = 2,    // scan tile ticket
+    CTR_SPARE = 2,
     CTR_WORK_P2G = 3,  // dynamic work counters of the persistent kernels
     CTR_WORK_GRID = 4,
     CTR_WORK_G2P = 5,

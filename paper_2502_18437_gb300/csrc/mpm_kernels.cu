@@ -1,7 +1,8 @@
 // Forward substep kernels of the MLS-MPM transfer loop (arXiv 2502.18437,
 // Algorithm 1) for GB300 (sm_103a):
 //   k_scan     brick histogram -> particle offsets, active particle-brick and
-//              node-brick lists (single-pass decoupled look-back scan)
+//              node-brick lists (tile sums kept by the key producers: no
+//              inter-CTA waits, empty tiles skipped)
 //   k_scatter  counting-sort scatter: permutation sorted slot -> particle
 //   k_p2g      P2G (Eq. 1, Eq. 8): balanced per-cell work items summed in
 //              registers into shared-memory 6^3 node windows per brick, flushed
@@ -18,13 +19,17 @@ namespace mpm {
 
 // ----------------------------------------------------------------- scan
 //
-// One tile = kScanTile (1024) consecutive bricks of the range.  Each brick
-// contributes (particles, is an active particle brick, is an active node brick);
-// a node brick is active when it or one of its 7 lower neighbours (-1 in any
-// subset of the axes) holds particles, since a particle's 3-node stencil reaches
-// at most 2 nodes beyond its base cell, i.e. into the next brick.  The key
-// producers (G2P, k_prepare) flag those bricks when the first particles enter a
-// brick, so the scan reads one count and one flag per brick and clears the flag.
+// A scan tile is 2^tile_shift consecutive bricks of one scene (tiles never
+// straddle scenes).  Each brick contributes (particles, is an active particle
+// brick, is an active node brick); a node brick is active when it or one of its
+// 7 lower neighbours (-1 in any subset of the axes) holds particles, since a
+// particle's 3-node stencil reaches at most 2 nodes beyond its base cell, i.e.
+// into the next brick.  The key producers (G2P, k_prepare) count particles per
+// brick, flag those node bricks when the first particles enter a brick, and add
+// each tile's three totals as they go.  So every CTA of the scan (one per tile
+// of the range) knows its exclusive prefix from the tile totals before it,
+// without waiting for another CTA; a tile with no active node brick has
+// nothing to write and returns at once.
 
 __device__ __forceinline__ int4 add4(int4 a, int4 b) { return make_int4(a.x + b.x, a.y + b.y, a.z + b.z, 0); }
 
@@ -37,169 +42,140 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(StepArgs a)
 {
     __shared__ int4 s_warp[kScanThreads / 32];
     __shared__ int4 s_prefix;
-    __shared__ int s_tile;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const SortBufs& sb = a.sb;
-    if (tid == 0) s_tile = atomicAdd(&sb.counters[CTR_TICKET], 1);
-    __syncthreads();
-    const int tile = s_tile;
-    const int n_tiles = (a.r.nbr + kScanTile - 1) / kScanTile;
-    if (tile == 0 && tid == 0) {
+    const int tile = a.r.t0 + blockIdx.x;
+    const bool last = blockIdx.x == a.r.nt - 1;
+    if (blockIdx.x == 0 && tid == 0) {
         sb.counters[CTR_WORK_P2G] = 0;
         sb.counters[CTR_WORK_GRID] = 0;
         sb.counters[CTR_WORK_G2P] = 0;
     }
+    const int4 own = __ldcg(&sb.tile_sum[tile]);
+    if (own.z == 0 && !last) return;  // no active node brick (hence no particle) here
 
-    const int first = a.r.bb0 + tile * kScanTile + tid * kScanItems;
-    const int end = a.r.bb0 + a.r.nbr;
-    // scene of the first item
-    int s = a.r.s0;
+    // exclusive prefix: the totals of the range's tiles before this one
+    int4 pre = make_int4(0, 0, 0, 0);
+    for (int t = a.r.t0 + tid; t < tile; t += kScanThreads) pre = add4(pre, __ldcg(&sb.tile_sum[t]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        pre.x += __shfl_xor_sync(kFull, pre.x, o);
+        pre.y += __shfl_xor_sync(kFull, pre.y, o);
+        pre.z += __shfl_xor_sync(kFull, pre.z, o);
+    }
+    if (lane == 0) s_warp[warp] = pre;
+    __syncthreads();
+    if (tid == 0) {
+        int4 p = make_int4(0, 0, 0, 0);
+#pragma unroll
+        for (int w = 0; w < kScanThreads / 32; ++w) p = add4(p, s_warp[w]);
+        s_prefix = p;
+        if (last) {
+            const int4 tot = add4(p, own);
+            if (tot.x == a.r.np) {
+                sb.counters[CTR_N_ACT] = tot.y;
+                sb.counters[CTR_N_NACT] = tot.z;
+            } else {
+                // histogram and particle count disagree: skip this substep's work
+                sb.counters[CTR_N_ACT] = 0;
+                sb.counters[CTR_N_NACT] = 0;
+                atomicOr(&a.err[a.r.s0], MPM_EBIT_INTERNAL);
+            }
+        }
+    }
+    __syncthreads();
+    if (own.z == 0) return;
+    int4 run = s_prefix;
+
+    // scene of the tile
+    int s;
     {
         int lo = a.r.s0, hi = a.r.s1 - 1;
         while (lo < hi) {
             int mid = (lo + hi + 1) >> 1;
-            if (a.scenes[mid].brick_base <= first) lo = mid;
+            if (a.scenes[mid].tile_base <= tile) lo = mid;
             else hi = mid - 1;
         }
         s = lo;
     }
-    int c[kScanItems], sc[kScanItems];
-    unsigned pf = 0, nf = 0;
-    int4 local = make_int4(0, 0, 0, 0);
+    const SceneDev& sc = a.scenes[s];
+    const int tb = 1 << sb.tile_shift;
+    const int b0 = sc.brick_base + (tile - sc.tile_base) * tb;
+    const int b1 = min(b0 + tb, sc.brick_base + sc.nb * sc.nb * sc.nb);
+    for (int chunk = b0; chunk < b1; chunk += kScanChunk) {
+        const int first = chunk + tid * kScanItems;
+        int c[kScanItems];
+        unsigned pf = 0, nf = 0;
+        int4 local = make_int4(0, 0, 0, 0);
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        const int b = first + k;
-        c[k] = 0;
-        sc[k] = s;
-        if (b < end) {
-            while (s + 1 < a.r.s1 && b >= a.scenes[s + 1].brick_base) ++s;
-            sc[k] = s;
-            c[k] = __ldcg(&sb.cnt[b]);
-            const int flag = __ldcg(&sb.nflag[b]);
-            if (flag) sb.nflag[b] = 0;  // consumed
-            const bool nact = c[k] > 0 || flag != 0;
-            if (c[k] > 0) pf |= 1u << k;
-            if (nact) nf |= 1u << k;
-            local.x += c[k];
+        for (int k = 0; k < kScanItems; ++k) {
+            const int b = first + k;
+            c[k] = 0;
+            if (b < b1) {
+                c[k] = __ldcg(&sb.cnt[b]);
+                const int flag = __ldcg(&sb.nflag[b]);
+                if (flag) sb.nflag[b] = 0;  // consumed
+                if (c[k] > 0) pf |= 1u << k;
+                if (flag) nf |= 1u << k;  // a non-empty brick always flags itself
+                local.x += c[k];
+            }
         }
-    }
-    local.y = __popc(pf);
-    local.z = __popc(nf);
-    // block exclusive scan of (particles, pbricks, nbricks)
-    int4 incl = local;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        int4 t = shfl_up4(incl, d);
-        if (lane >= d) incl = add4(incl, t);
-    }
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        int4 w = lane < kScanThreads / 32 ? s_warp[lane] : make_int4(0, 0, 0, 0);
+        local.y = __popc(pf);
+        local.z = __popc(nf);
+        // block exclusive scan of (particles, pbricks, nbricks)
+        int4 incl = local;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            int4 t = shfl_up4(w, d);
-            if (lane >= d) w = add4(w, t);
+            int4 t = shfl_up4(incl, d);
+            if (lane >= d) incl = add4(incl, t);
         }
-        if (lane < kScanThreads / 32) s_warp[lane] = w;  // inclusive over warps
-    }
-    __syncthreads();
-    int4 excl = make_int4(incl.x - local.x, incl.y - local.y, incl.z - local.z, 0);
-    if (warp > 0) excl = add4(excl, s_warp[warp - 1]);
-    // decoupled look-back across tiles, 32 predecessors per step (warp 0)
-    if (warp == 0) {
-        const int4 agg = s_warp[kScanThreads / 32 - 1];
-        int4 prefix = make_int4(0, 0, 0, 0);
-        if (tile == 0) {
-            if (lane == 0) {
-                sb.tile_incl[0] = agg;
-                __threadfence();
-                st_release(&sb.tile_status[0], 2u);
-            }
-        } else {
-            if (lane == 0) {
-                sb.tile_agg[tile] = agg;
-                __threadfence();
-                st_release(&sb.tile_status[tile], 1u);
-            }
-            int top = tile - 1;
-            int spins = 0;
-            for (;;) {
-                const int idx = top - lane;
-                const unsigned st = idx >= 0 ? ld_acquire(&sb.tile_status[idx]) : 2u;  // before tile 0: zero
-                const unsigned m2 = __ballot_sync(kFull, st == 2u);
-                const unsigned m0 = __ballot_sync(kFull, st == 0u);
-                const int first2 = m2 ? __ffs(m2) - 1 : 32;
-                const unsigned need = first2 >= 31 ? kFull : ((2u << first2) - 1u);  // lanes 0..first2
-                if (m0 & need) {
-                    if (++spins > (1 << 22)) {  // a predecessor never published: flag and give up
-                        if (lane == 0) atomicOr(&a.err[a.r.s0], MPM_EBIT_TIMEOUT);
-                        break;
-                    }
-                    __nanosleep(20);
-                    continue;
-                }
-                int4 v = make_int4(0, 0, 0, 0);
-                if (lane < first2 && idx >= 0) v = __ldcg(&sb.tile_agg[idx]);
-                if (lane == first2 && idx >= 0) v = __ldcg(&sb.tile_incl[idx]);
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int4 w = lane < kScanThreads / 32 ? s_warp[lane] : make_int4(0, 0, 0, 0);
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    v.x += __shfl_xor_sync(kFull, v.x, o);
-                    v.y += __shfl_xor_sync(kFull, v.y, o);
-                    v.z += __shfl_xor_sync(kFull, v.z, o);
-                }
-                prefix = add4(prefix, v);
-                if (m2) break;
-                top -= 32;
+            for (int d = 1; d < 32; d <<= 1) {
+                int4 t = shfl_up4(w, d);
+                if (lane >= d) w = add4(w, t);
             }
-            if (lane == 0) {
-                sb.tile_incl[tile] = add4(prefix, agg);
-                __threadfence();
-                st_release(&sb.tile_status[tile], 2u);
-            }
+            if (lane < kScanThreads / 32) s_warp[lane] = w;  // inclusive over warps
         }
-        if (lane == 0) {
-            s_prefix = prefix;
-            if (tile == n_tiles - 1) {
-                const int4 tot = add4(prefix, agg);
-                if (tot.x == a.r.np) {
-                    sb.counters[CTR_N_ACT] = tot.y;
-                    sb.counters[CTR_N_NACT] = tot.z;
-                } else {
-                    // histogram and particle count disagree: skip this substep's work
-                    sb.counters[CTR_N_ACT] = 0;
-                    sb.counters[CTR_N_NACT] = 0;
-                    atomicOr(&a.err[a.r.s0], MPM_EBIT_INTERNAL);
-                }
-            }
+        __syncthreads();
+        int4 excl = make_int4(incl.x - local.x, incl.y - local.y, incl.z - local.z, 0);
+        if (warp > 0) excl = add4(excl, s_warp[warp - 1]);
+        excl = add4(excl, run);
+        int po = a.r.p0 + excl.x, pi = excl.y, ni = excl.z;
+        if (pi + local.y > a.r.nbr || ni + local.z > a.r.nbr) {  // tile sums out of step with the bricks
+            atomicOr(&a.err[a.r.s0], MPM_EBIT_INTERNAL);
+            pf = nf = 0u;
         }
-    }
-    __syncthreads();
-    excl = add4(excl, s_prefix);
-    int po = a.r.p0 + excl.x, pi = excl.y, ni = excl.z;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        const int b = first + k;
-        if (pf & (1u << k)) {
-            sb.off[b] = po;
-            sb.act_brick[pi] = b;
-            sb.act_start[pi] = po;
-            sb.act_count[pi] = c[k];
-            sb.act_scene[pi] = sc[k];
-            ++pi;
+        for (int k = 0; k < kScanItems; ++k) {
+            const int b = first + k;
+            if (pf & (1u << k)) {
+                sb.off[b] = po;
+                sb.act_brick[pi] = b;
+                sb.act_start[pi] = po;
+                sb.act_count[pi] = c[k];
+                sb.act_scene[pi] = s;
+                ++pi;
+            }
+            if (nf & (1u << k)) {
+                sb.nact_brick[ni] = b;
+                sb.nact_scene[ni] = s;
+                ++ni;
+            }
+            po += c[k];
         }
-        if (nf & (1u << k)) {
-            sb.nact_brick[ni] = b;
-            sb.nact_scene[ni] = sc[k];
-            ++ni;
-        }
-        po += c[k];
+        run = add4(run, s_warp[kScanThreads / 32 - 1]);
+        __syncthreads();  // s_warp is rewritten by the next chunk
     }
 }
 
-// Counting-sort scatter; also clears the scan's tile state for the next substep.
-// write_perm = 0 only clears (the adjoint reuses a recorded permutation).
-__global__ void k_scatter(StepArgs a, int n_tiles, int write_perm)
+// Counting-sort scatter; also clears the range's tile sums for the next
+// substep (the scan has read them).  write_perm = 0 only clears (the adjoint
+// reuses a recorded permutation).
+__global__ void k_scatter(StepArgs a, int write_perm)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = a.r.p0 + g;
@@ -213,8 +189,7 @@ __global__ void k_scatter(StepArgs a, int n_tiles, int write_perm)
             atomicOr(&a.err[a.r.s0], MPM_EBIT_INTERNAL);
         }
     }
-    if (g < n_tiles) a.sb.tile_status[g] = 0u;
-    if (g == 0) a.sb.counters[CTR_TICKET] = 0;
+    if (g < a.r.nt) a.sb.tile_sum[a.r.t0 + g] = make_int4(0, 0, 0, 0);
 }
 
 // Keys and ranks of the stored particles after the host changed positions
@@ -241,7 +216,7 @@ __global__ void k_prepare(StepArgs a, PState st)
         key = cell_key(sc, st.x[i], st.x[a.cap + i], st.x[2 * a.cap + i], ood);
         if (ood) ebits |= MPM_EBIT_OUT_OF_DOMAIN;
     }
-    const int rank = aggregated_rank_mark(a.sb.cnt, a.sb.nflag, sc, key >> 6, valid);
+    const int rank = aggregated_rank_mark(a.sb, sc, key >> 6, valid);
     if (valid) {
         a.sb.key[i] = key;
         a.sb.rank[i] = rank;
@@ -965,7 +940,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_g2p(StepArgs a)
                 key = cell_key(sc, o.x[0], o.x[1], o.x[2], ood);
                 if (ood && !(ebits & MPM_EBIT_NONFINITE)) ebits |= MPM_EBIT_OUT_OF_DOMAIN;
             }
-            const int rank = aggregated_rank_mark(a.sb.cnt, a.sb.nflag, sc, key >> 6, valid);
+            const int rank = aggregated_rank_mark(a.sb, sc, key >> 6, valid);
             if (valid) {
                 a.sb.key[start + k] = key;
                 a.sb.rank[start + k] = rank;
@@ -1076,7 +1051,7 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_g2p2g(StepArgs a)
                             }
                 }
             }
-            const int rank = aggregated_rank_mark(a.sb.cnt, a.sb.nflag, sc, key >> 6, valid);
+            const int rank = aggregated_rank_mark(a.sb, sc, key >> 6, valid);
             if (valid) {
                 a.sb.key[start + k] = key;
                 a.sb.rank[start + k] = rank;
@@ -1195,12 +1170,11 @@ cudaError_t launch_prepare(const StepArgs& a, const PState& st, cudaStream_t s)
 
 cudaError_t launch_sort(const StepArgs& a, cudaStream_t s, bool write_perm)
 {
-    const int n_tiles = (a.r.nbr + kScanTile - 1) / kScanTile;
-    k_scan<<<n_tiles, kScanThreads, 0, s>>>(a);
+    k_scan<<<a.r.nt, kScanThreads, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int work = a.r.np > n_tiles ? a.r.np : n_tiles;
-    k_scatter<<<n_blocks(work, 256), 256, 0, s>>>(a, n_tiles, write_perm ? 1 : 0);
+    const int work = a.r.np > a.r.nt ? a.r.np : a.r.nt;
+    k_scatter<<<n_blocks(work, 256), 256, 0, s>>>(a, write_perm ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -8,6 +8,7 @@ namespace mpm {
 struct Range {
     int s0, s1;     // scene range [s0, s1)
     int bb0, nbr;   // global brick range [bb0, bb0 + nbr)
+    int t0, nt;     // scan tile range [t0, t0 + nt)
     int p0, np;     // particle range [p0, p0 + np)
 };
 
@@ -27,9 +28,10 @@ struct SortBufs {
     int* nact_brick;// [bricks] active node bricks
     int* nact_scene;
     int* counters;  // [CTR_COUNT]
-    unsigned* tile_status;
-    int4* tile_agg;
-    int4* tile_incl;
+    int4* tile_sum; // [tiles] per scan tile (particles, active particle bricks, active node
+                    // bricks) of the next substep, added up by the key producers,
+                    // read by the scan and cleared by the scatter
+    int tile_shift; // log2 of the bricks per scan tile
 };
 
 struct StepArgs {
@@ -64,7 +66,7 @@ constexpr int kStateFloats = 32;  // x3 v3 C9 F9 tau6 mu lam (+ int id)
 constexpr int kP2GThreads = 192;  // 64 cells x 3 node slices
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 4;
-constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr int kScanChunk = kScanThreads * kScanItems;  // bricks per pass of a scan CTA
 
 cudaError_t launch_prepare(const StepArgs& a, const PState& st, cudaStream_t s);
 cudaError_t launch_sort(const StepArgs& a, cudaStream_t s, bool write_perm = true);

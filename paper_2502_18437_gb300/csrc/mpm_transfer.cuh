@@ -15,18 +15,6 @@ __device__ __forceinline__ unsigned smem_u32(const void* p)
     return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
-{
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release(unsigned* p, unsigned v)
-{
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 __device__ __forceinline__ void red_add_v4(float4* addr, float a, float b, float c, float d)
 {
     asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
@@ -96,46 +84,42 @@ __device__ __forceinline__ int cell_key(const SceneDev& sc, float x0, float x1, 
     return brick * 64 + ((c0 & 3) * 16 + (c1 & 3) * 4 + (c2 & 3));
 }
 
-// Warp-aggregated rank: lanes with the same key get consecutive ranks from one
-// atomic.  Must be called by all 32 lanes; `valid` marks lanes with a particle.
-__device__ __forceinline__ int aggregated_rank(int* cnt, int key, bool valid)
+// Warp-aggregated rank: lanes with the same brick get consecutive ranks from
+// one atomic (all 32 lanes call it; `valid` marks lanes with a particle).  It
+// also keeps the scan's bookkeeping of the next substep:
+//  - the brick's particle count (the rank base) and its scan tile's sums;
+//  - for the first warp to add particles to a brick, the brick and its 7 upper
+//    neighbours (+1 in any subset of the axes) are flagged as node bricks the
+//    scan must activate (a particle's 3-node stencil reaches at most 2 nodes
+//    past its base cell, i.e. into the next brick).  Each flag is set with an
+//    exchange, so that its tile counts every node brick exactly once.
+// brick is the global brick index of the key.
+__device__ __forceinline__ int aggregated_rank_mark(const SortBufs& sb, const SceneDev& sc, int brick, bool valid)
 {
     const unsigned active = __ballot_sync(kFull, valid);
     int rank = 0;
-    const unsigned peers = __match_any_sync(kFull, valid ? key : -1) & active;
-    if (valid) {
-        const int lane = threadIdx.x & 31;
-        const int leader = __ffs(peers) - 1;
-        int base = 0;
-        if (lane == leader) base = atomicAdd(&cnt[key], __popc(peers));
-        base = __shfl_sync(peers, base, leader);
-        rank = base + __popc(peers & ((1u << lane) - 1u));
-    }
-    return rank;
-}
-
-// aggregated_rank that also marks, for the first warp to add particles to a
-// brick in this substep, the brick and its 7 upper neighbours (+1 in any subset
-// of the axes) as node bricks the scan must activate: a particle's 3-node
-// stencil reaches at most 2 nodes past its base cell, i.e. into the next brick.
-__device__ __forceinline__ int aggregated_rank_mark(int* cnt, int* nflag, const SceneDev& sc, int key, bool valid)
-{
-    const unsigned active = __ballot_sync(kFull, valid);
-    int rank = 0;
-    const unsigned peers = __match_any_sync(kFull, valid ? key : -1) & active;
+    const unsigned peers = __match_any_sync(kFull, valid ? brick : -1) & active;
     if (valid) {
         const int lane = threadIdx.x & 31;
         const int leader = __ffs(peers) - 1;
         int base = 0;
         if (lane == leader) {
-            base = atomicAdd(&cnt[key], __popc(peers));
+            const int np = __popc(peers);
+            const int lb = brick - sc.brick_base;
+            int4* ts = sb.tile_sum + sc.tile_base;
+            base = atomicAdd(&sb.cnt[brick], np);
+            atomicAdd(&ts[lb >> sb.tile_shift].x, np);
             if (base == 0) {
-                const int nb = sc.nb, lb = key - sc.brick_base;
+                atomicAdd(&ts[lb >> sb.tile_shift].y, 1);
+                const int nb = sc.nb;
                 const int bx = lb / (nb * nb), by = (lb / nb) % nb, bz = lb % nb;
 #pragma unroll
                 for (int o = 0; o < 8; ++o) {
                     const int ex = bx + (o >> 2), ey = by + ((o >> 1) & 1), ez = bz + (o & 1);
-                    if (ex < nb && ey < nb && ez < nb) nflag[sc.brick_base + (ex * nb + ey) * nb + ez] = 1;
+                    if (ex < nb && ey < nb && ez < nb) {
+                        const int ln = (ex * nb + ey) * nb + ez;
+                        if (atomicExch(&sb.nflag[sc.brick_base + ln], 1) == 0) atomicAdd(&ts[ln >> sb.tile_shift].z, 1);
+                    }
                 }
             }
         }
