@@ -133,8 +133,11 @@ __device__ __forceinline__ void jacobi_rot(float& app, float& aqq, float& apq, f
                                            float& v0p, float& v0q, float& v1p, float& v1q, float& v2p,
                                            float& v2q)
 {
-    // already converged to single precision (also keeps b^2 clear of underflow)
-    if (!(fabsf(apq) > 1e-10f * fmaxf(fabsf(app), fabsf(aqq)))) return;
+    // converged: an off-diagonal below half a unit roundoff of the larger diagonal
+    // entry (2^-25) is smaller than the rounding error of that entry itself, so the
+    // rotation would not change the result in single precision (this also keeps
+    // b^2 clear of underflow)
+    if (!(fabsf(apq) > 2.98e-8f * fmaxf(fabsf(app), fabsf(aqq)))) return;
     const float d = aqq - app, b = 2.0f * apq;
     // scale by max(|d|, |b|) > 0 so that d^2 + b^2 neither underflows nor overflows
     const float inv = __fdividef(1.0f, fmaxf(fabsf(d), fabsf(b)));
