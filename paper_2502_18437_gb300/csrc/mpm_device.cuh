@@ -139,11 +139,10 @@ __device__ __forceinline__ void jacobi_rot(float& app, float& aqq, float& apq, f
     // b^2 clear of underflow)
     if (!(fabsf(apq) > 2.98e-8f * fmaxf(fabsf(app), fabsf(aqq)))) return;
     const float d = aqq - app, b = 2.0f * apq;
-    // scale by max(|d|, |b|) > 0 so that d^2 + b^2 neither underflows nor overflows
-    const float inv = __fdividef(1.0f, fmaxf(fabsf(d), fabsf(b)));
-    const float ds = d * inv, bs = b * inv;
-    const float den = fabsf(ds) + approx_sqrt(__fmaf_rn(ds, ds, bs * bs));
-    const float t = __fdividef(d >= 0.0f ? bs : -bs, den);
+    // |d| + sqrt(d^2 + b^2) >= |b| > 0; the max keeps that true where b^2 underflows
+    // (only for a degenerate F, whose entries would be below ~1e-9)
+    const float den = fmaxf(fabsf(d) + approx_sqrt(__fmaf_rn(d, d, b * b)), fabsf(b));
+    const float t = __fdividef(d >= 0.0f ? b : -b, den);
     const float c = rsqrtf(__fmaf_rn(t, t, 1.0f));
     const float s = t * c;
     app = __fmaf_rn(-t, apq, app);

@@ -375,22 +375,22 @@ __global__ void __launch_bounds__(kP2GThreads, 4) k_p2g(StepArgs a)
             }
             __syncthreads();
             // B: item sums in registers, then staged
-            float acc_w[9], acc_p[9][3];
+            float2 acc_a[9], acc_b[9];  // (p_x, p_y), (p_z, weight)
 #pragma unroll
-            for (int q = 0; q < 9; ++q) { acc_w[q] = 0.f; acc_p[q][0] = acc_p[q][1] = acc_p[q][2] = 0.f; }
+            for (int q = 0; q < 9; ++q) acc_a[q] = acc_b[q] = make_float2(0.f, 0.f);
             if (t < n_items)
                 item_accumulate<kP2GSlots>(rec, inter ? (t < 32 ? 0 : kP2GSlotPitch * rows0) + (t & 31) : it_beg[t],
                                            inter ? kP2GSlotPitch : 1,
-                                           it_len[t], slice, acc_w, acc_p);
+                                           it_len[t], slice, acc_a, acc_b);
             __syncthreads();
             if (t < n_items) {
                 float* st = stage + slice * 64 + t;
 #pragma unroll
                 for (int q = 0; q < 9; ++q) {
-                    st[(4 * q) * 192] = acc_w[q] * m;
-                    st[(4 * q + 1) * 192] = acc_p[q][0];
-                    st[(4 * q + 2) * 192] = acc_p[q][1];
-                    st[(4 * q + 3) * 192] = acc_p[q][2];
+                    st[(4 * q) * 192] = acc_b[q].y * m;
+                    st[(4 * q + 1) * 192] = acc_a[q].x;
+                    st[(4 * q + 2) * 192] = acc_a[q].y;
+                    st[(4 * q + 3) * 192] = acc_b[q].x;
                 }
             }
             __syncthreads();

@@ -348,10 +348,11 @@ __device__ __forceinline__ void put_item_record(float (*rec)[N], int k, const fl
 // the item's particles, whose records sit at slots slot0, slot0 + stride, ...,
 // to the 9 nodes cell + (slice, j, k) in registers.  The weights follow the
 // quadratic B-spline of bspline(): slice i needs w_i(f_x) only, written as
-// alpha + beta (f - gamma)^2.
+// alpha + beta (f - gamma)^2.  The sums are kept in pairs, (p_x, p_y) in
+// acc_a and (p_z, weight) in acc_b, each updated by one paired FMA.
 template <int N>
 __device__ __forceinline__ void item_accumulate(const float (*rec)[N], int slot0, int stride, int len, int slice,
-                                                float acc_w[9], float acc_p[9][3])
+                                                float2 acc_a[9], float2 acc_b[9])
 {
     const float si = (float)slice;
     const float gam = slice == 0 ? 1.5f : (slice == 1 ? 1.0f : 0.5f);
@@ -364,21 +365,26 @@ __device__ __forceinline__ void item_accumulate(const float (*rec)[N], int slot0
         float wy[3], wz[3];
         bspline(fy, wy);
         bspline(fz, wz);
-        const float r0 = rec[3][k] + si * rec[6][k], r1 = rec[4][k] + si * rec[9][k], r2 = rec[5][k] + si * rec[12][k];
-        const float a01 = rec[7][k], a11 = rec[10][k], a21 = rec[13][k];
-        const float a02 = rec[8][k], a12 = rec[11][k], a22 = rec[14][k];
+        // value of node (slice, jj, kk): r + a1 jj + a2 kk (r includes the slice's term)
+        const float2 r01 = make_float2(__fmaf_rn(si, rec[6][k], rec[3][k]), __fmaf_rn(si, rec[9][k], rec[4][k]));
+        const float r2 = __fmaf_rn(si, rec[12][k], rec[5][k]);
+        const float2 a1 = make_float2(rec[7][k], rec[10][k]), a2 = make_float2(rec[8][k], rec[11][k]);
+        const float a21 = rec[13][k], a22 = rec[14][k];
 #pragma unroll
         for (int jj = 0; jj < 3; ++jj) {
             const float wij = wi * wy[jj];
-            const float s0 = r0 + a01 * jj, s1 = r1 + a11 * jj, s2 = r2 + a21 * jj;
+            const float fj = (float)jj;
+            const float2 s01 = jj == 0 ? r01 : __ffma2_rn(make_float2(fj, fj), a1, r01);
+            const float s2 = __fmaf_rn(a21, fj, r2);
 #pragma unroll
             for (int kk = 0; kk < 3; ++kk) {
                 const float W = wij * wz[kk];
+                const float fk = (float)kk;
                 const int q = jj * 3 + kk;
-                acc_w[q] += W;
-                acc_p[q][0] += W * (s0 + a02 * kk);
-                acc_p[q][1] += W * (s1 + a12 * kk);
-                acc_p[q][2] += W * (s2 + a22 * kk);
+                const float2 v01 = kk == 0 ? s01 : __ffma2_rn(make_float2(fk, fk), a2, s01);
+                const float2 v2w = make_float2(__fmaf_rn(a22, fk, s2), 1.0f);
+                acc_a[q] = __ffma2_rn(make_float2(W, W), v01, acc_a[q]);
+                acc_b[q] = __ffma2_rn(make_float2(W, W), v2w, acc_b[q]);
             }
         }
     }
