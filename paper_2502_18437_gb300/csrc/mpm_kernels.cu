@@ -238,7 +238,7 @@ __global__ void k_prepare(StepArgs a, PState st)
 //      the 32 lanes of a warp read 32 consecutive words in phase B and the
 //      particles of one item (consecutive lanes here when the input is in cell
 //      order) write to different banks; a pass whose two item warps need more
-//      than kP2GSlots slots falls back to cell-sorted slots.  The pass's slots
+//      than the pass's record slots falls back to cell-sorted slots.  The pass's slots
 //      of the permutation are rewritten in cell order (cell_order), so that G2P
 //      gathers a warp's 27-node stencils from a few neighbouring cells;
 //   B.  thread (item, slice i) sums, in registers, the contributions of its
@@ -246,28 +246,37 @@ __global__ void k_prepare(StepArgs a, PState st)
 //   C.  thread (cell, slice i) adds the staged sums of its cell's items and
 //      adds them to slice i's copy of the 6^3 window: the 64 cells of a slice
 //      never write the same node at once, so no atomics are needed.
-// At the end of the brick the window is added to HBM with one vector reduction
-// per node.
+// At the end of the pass the window is added to HBM with one vector reduction
+// per node.  Stage and windows reuse the record slots.
 
 constexpr int kP2GSlotPitch = 33;  // 32 lanes + 1: rows of one item fall in different banks
-constexpr int kP2GSlots = 24 * kP2GSlotPitch;
+// record slots of a pass of PER x 192 particles (the rows of the interleaved
+// layout; 768-particle passes need 24).  A smaller record area leaves more of
+// the SM's shared storage to L1.
+template <int PER>
+struct P2GShape {
+    static constexpr int slots = (PER == 4 ? 24 : 21) * kP2GSlotPitch;
+};
 constexpr int kSliceNodes = 4 * 36;  // node planes x = slice .. slice + 3 of the 6^3 window
 constexpr int kStageFloats = 36 * 3 * 64;  // (9 nodes x 4 values) x 3 slices x 64 items
-static_assert(kStageFloats <= kItemRecFields * kP2GSlots, "the stage reuses the record slots");
+constexpr int kWinFloats = 3 * 4 * kSliceNodes;  // the slices' windows, after the stage
 
 template <int PER>
 __global__ void __launch_bounds__(kP2GThreads, 4) k_p2g(StepArgs a)
 {
     constexpr int CHUNK = PER * kP2GThreads;
+    constexpr int kP2GSlots = P2GShape<PER>::slots;
     static_assert(CHUNK <= kP2GSlots, "a pass fits the record slots");
+    static_assert(kStageFloats + kWinFloats <= kItemRecFields * kP2GSlots, "stage and windows reuse the record slots");
     extern __shared__ __align__(16) float rec_dyn[];
     float(*rec)[kP2GSlots] = reinterpret_cast<float(*)[kP2GSlots]>(rec_dyn);  // [kItemRecFields][kP2GSlots]
-    float* stage = rec_dyn;  // [36][3][64], written once phase B has read every record
+    // written once phase B has read every record: the staged item sums [36][3][64]
+    // and one window per slice (slice i writes node planes x = i..i+3 only, so the
+    // slices' writes never collide), added to HBM at the end of each pass
+    float* stage = rec_dyn;
+    float(*win)[4][kSliceNodes] = reinterpret_cast<float(*)[4][kSliceNodes]>(rec_dyn + kStageFloats);
     __shared__ int cell_cnt[64], cell_off[65];
     __shared__ short it_cell[64], it_beg[64], it_len[64], c_full[64], c_nf[64], c_rem[64];
-    // one window per slice (slice i writes node planes x = i..i+3 only): the
-    // slices' writes never collide
-    __shared__ float win[3][4][kSliceNodes];
     __shared__ int s_item, s_nitems, s_len[3];
     const int tid = threadIdx.x;
     const int t = tid & 63, slice = tid >> 6;
@@ -275,7 +284,6 @@ __global__ void __launch_bounds__(kP2GThreads, 4) k_p2g(StepArgs a)
     const int cap = a.cap;
     for (;;) {
         if (tid == 0) s_item = atomicAdd(&a.sb.counters[CTR_WORK_P2G], 1);
-        for (int q = tid; q < 12 * kSliceNodes; q += kP2GThreads) (&win[0][0][0])[q] = 0.0f;
         if (tid < 64) cell_cnt[tid] = 0;
         __syncthreads();
         const int item = s_item;
@@ -383,6 +391,7 @@ __global__ void __launch_bounds__(kP2GThreads, 4) k_p2g(StepArgs a)
                                            inter ? kP2GSlotPitch : 1,
                                            it_len[t], slice, acc_a, acc_b);
             __syncthreads();
+            for (int q = tid; q < kWinFloats; q += kP2GThreads) (&win[0][0][0])[q] = 0.0f;
             if (t < n_items) {
                 float* st = stage + slice * 64 + t;
 #pragma unroll
@@ -426,21 +435,23 @@ __global__ void __launch_bounds__(kP2GThreads, 4) k_p2g(StepArgs a)
                 }
             }
             __syncthreads();
-        }
-        for (int q = tid; q < kWinNodes; q += kP2GThreads) {
-            const int X = q / 36, yz = q % 36;
-            float s4[4] = {0.f, 0.f, 0.f, 0.f};
+            // the pass's window to HBM, one vector reduction per node (read before
+            // the next pass's records overwrite it: two barriers away)
+            for (int q = tid; q < kWinNodes; q += kP2GThreads) {
+                const int X = q / 36, yz = q % 36;
+                float s4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int sl = 0; sl < 3; ++sl) {
-                const int cx = X - sl;
-                if (cx < 0 || cx > 3) continue;
+                for (int sl = 0; sl < 3; ++sl) {
+                    const int cx = X - sl;
+                    if (cx < 0 || cx > 3) continue;
 #pragma unroll
-                for (int comp = 0; comp < 4; ++comp) s4[comp] += win[sl][comp][cx * 36 + yz];
+                    for (int comp = 0; comp < 4; ++comp) s4[comp] += win[sl][comp][cx * 36 + yz];
+                }
+                if (s4[0] == 0.0f) continue;
+                const int gi = ox + X, gj = oy + yz / 6, gk = oz + yz % 6;
+                if (gi >= n || gj >= n || gk >= n) continue;
+                red_add_v4(&a.G[node_index(sc, gi, gj, gk)], s4[0], s4[1], s4[2], s4[3]);
             }
-            if (s4[0] == 0.0f) continue;
-            const int gi = ox + X, gj = oy + yz / 6, gk = oz + yz % 6;
-            if (gi >= n || gj >= n || gk >= n) continue;
-            red_add_v4(&a.G[node_index(sc, gi, gj, gk)], s4[0], s4[1], s4[2], s4[3]);
         }
         if (ebits) atomicOr(&a.err[scene], ebits);
         __syncthreads();
@@ -1179,7 +1190,7 @@ cudaError_t launch_sort(const StepArgs& a, cudaStream_t s, bool write_perm)
 }
 
 template <int PER>
-static constexpr size_t p2g_dyn_smem() { return sizeof(float) * kItemRecFields * kP2GSlots; }
+static constexpr size_t p2g_dyn_smem() { return sizeof(float) * kItemRecFields * P2GShape<PER>::slots; }
 
 cudaError_t prepare_p2g()
 {
