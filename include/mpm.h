@@ -93,7 +93,7 @@ enum {
     MPM_OPT_PHASE_TIMING = 7,   /* 0/1: record CUDA events around each phase of every
                                    substep (forces direct launches); see mpm_phase_stats */
     MPM_OPT_P2G_CHUNK = 8,      /* particles staged per pass of the P2G kernel: 384,
-                                   576 (default) or 768                             */
+                                   576 or 768 (default)                             */
     MPM_OPT_FUSED = 9,          /* 1: fuse each substep's G2P with the next substep's
                                    P2G; 0 (default): separate P2G and G2P kernels */
     MPM_OPT_G2P_REGS64 = 10     /* 1 (default): G2P variant limited to 64 registers

@@ -57,7 +57,7 @@ struct mpm_ctx {
     // options
     int use_graphs = 1;
     int launch_mode = 0;
-    int p2g_chunk = 3 * mpm::kP2GThreads;
+    int p2g_chunk = 4 * mpm::kP2GThreads;
     int g2p_threads = 128;
     int g2p_regs64 = 1;
     int ctas_per_sm = 0;
