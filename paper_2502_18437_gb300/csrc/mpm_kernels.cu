@@ -193,9 +193,18 @@ __global__ void k_scatter(StepArgs a, int write_perm)
 }
 
 // Keys and ranks of the stored particles after the host changed positions
-// (new particles, state writes).
-__global__ void k_prepare(StepArgs a, PState st)
+// (new particles, state writes).  Stored particles may be in any order here, so
+// the tiles' particle counts are first summed per block in shared memory (with
+// at most kPrepTiles tiles in the range; else each warp adds its own).
+constexpr int kPrepTiles = 2048;
+
+__global__ void __launch_bounds__(256) k_prepare(StepArgs a, PState st)
 {
+    __shared__ int s_tile[kPrepTiles];
+    const bool block_sums = a.r.nt <= kPrepTiles;
+    if (block_sums)
+        for (int t = threadIdx.x; t < a.r.nt; t += blockDim.x) s_tile[t] = 0;
+    __syncthreads();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = a.r.p0 + g;
     const bool valid = g < a.r.np;
@@ -216,11 +225,18 @@ __global__ void k_prepare(StepArgs a, PState st)
         key = cell_key(sc, st.x[i], st.x[a.cap + i], st.x[2 * a.cap + i], ood);
         if (ood) ebits |= MPM_EBIT_OUT_OF_DOMAIN;
     }
-    const int rank = aggregated_rank_mark(a.sb, sc, key >> 6, valid);
+    const int rank = aggregated_rank_mark(a.sb, sc, key >> 6, valid, !block_sums);
     if (valid) {
         a.sb.key[i] = key;
         a.sb.rank[i] = rank;
         if (ebits) atomicOr(&a.err[scene], ebits);
+        if (block_sums)
+            atomicAdd(&s_tile[sc.tile_base + (((key >> 6) - sc.brick_base) >> a.sb.tile_shift) - a.r.t0], 1);
+    }
+    if (block_sums) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < a.r.nt; t += blockDim.x)
+            if (s_tile[t]) atomicAdd(&a.sb.tile_sum[a.r.t0 + t].x, s_tile[t]);
     }
 }
 

@@ -93,8 +93,10 @@ __device__ __forceinline__ int cell_key(const SceneDev& sc, float x0, float x1, 
 //    scan must activate (a particle's 3-node stencil reaches at most 2 nodes
 //    past its base cell, i.e. into the next brick).  Each flag is set with an
 //    exchange, so that its tile counts every node brick exactly once.
-// brick is the global brick index of the key.
-__device__ __forceinline__ int aggregated_rank_mark(const SortBufs& sb, const SceneDev& sc, int brick, bool valid)
+// brick is the global brick index of the key.  add_x = false leaves the tile's
+// particle count to the caller (which then aggregates it itself).
+__device__ __forceinline__ int aggregated_rank_mark(const SortBufs& sb, const SceneDev& sc, int brick, bool valid,
+                                                    bool add_x = true)
 {
     const unsigned active = __ballot_sync(kFull, valid);
     int rank = 0;
@@ -108,7 +110,7 @@ __device__ __forceinline__ int aggregated_rank_mark(const SortBufs& sb, const Sc
             const int lb = brick - sc.brick_base;
             int4* ts = sb.tile_sum + sc.tile_base;
             base = atomicAdd(&sb.cnt[brick], np);
-            atomicAdd(&ts[lb >> sb.tile_shift].x, np);
+            if (add_x) atomicAdd(&ts[lb >> sb.tile_shift].x, np);
             if (base == 0) {
                 atomicAdd(&ts[lb >> sb.tile_shift].y, 1);
                 const int nb = sc.nb;
