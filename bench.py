@@ -200,17 +200,18 @@ def algorithmic_bytes(N, bricks, active_nodes, pp_mat=False):
     """Bytes each phase must move at least once per substep (the table of the
     kernels and their bounds):
       sort  scan: brick count + node flag (8 B per brick of the grid); scatter:
-            key, rank and the brick offset read, slot written (16 B per particle)
-      p2g   perm 4 + x 12 + v 12 + C 36 + tau 24 read, perm 4 rewritten in cell
-            order (92 B per particle) + one 16-B reduction per active node
+            key, rank and the brick offset read, slot and its cell written (17 B
+            per particle)
+      p2g   perm 4 + cell 1 + x 12 + v 12 + C 36 + tau 24 read, perm 4 rewritten
+            in cell order (93 B per particle) + one 16-B reduction per active node
       grid  (m, mv) read, (v, m) written, (m, mv) cleared: 48 B per active node
       g2p   perm 4 + x 12 + F 36 + id 4 read; x, v, C, F 96 + tau 24 + id 4 +
             key, rank 8 written (188 B per particle; + mu, lam 16 with
             per-particle materials) + the velocity window, 16 B per active node"""
     extra = 16 if pp_mat else 0
     return {
-        "sort": 8 * bricks + 16 * N,
-        "p2g": 92 * N + 16 * active_nodes,
+        "sort": 8 * bricks + 17 * N,
+        "p2g": 93 * N + 16 * active_nodes,
         "grid": 48 * active_nodes,
         "g2p": (188 + extra) * N + 16 * active_nodes,
     }
