@@ -817,13 +817,27 @@ struct G2POut {
     float x[3], v[3], C[9], t6[6];
 };
 
+__device__ __forceinline__ void cp_async4(float* dst, const float* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Staged mode (sX != nullptr): x and F of particle p were copied into
+// sX[d * stride] and sF[q * stride] by cp.async one particle ahead; this call
+// starts the copies of particle pnext (when >= 0) as soon as its own values
+// are out of the buffers: x after the gather, F after the F update.
 __device__ __forceinline__ unsigned g2p_particle(const StepArgs& a, const SceneDev& sc, const float4* lin, int p, int s,
-                                                 int ox, int oy, int oz, G2POut& o)
+                                                 int ox, int oy, int oz, G2POut& o, float* sX = nullptr,
+                                                 float* sF = nullptr, int stride = 0, int pnext = -1)
 {
     const int cap = a.cap, n = sc.n;
     const float fn = (float)n, dt = a.dt;
     unsigned ebits = 0;
-    const float x0 = a.in.x[p], x1 = a.in.x[cap + p], x2 = a.in.x[2 * cap + p];
+    if (sX) cp_async_wait_all();
+    const float x0 = sX ? sX[0] : a.in.x[p], x1 = sX ? sX[stride] : a.in.x[cap + p],
+                x2 = sX ? sX[2 * stride] : a.in.x[2 * cap + p];
     int bc[3];
     float f[3], w[9];
     particle_weights(x0, x1, x2, n, bc, f, w);
@@ -869,6 +883,10 @@ __device__ __forceinline__ unsigned g2p_particle(const StepArgs& a, const SceneD
         B[3 * r + 2] = wx[0] * Bz[0][r] + wx[1] * Bz[1][r] + wx[2] * Bz[2][r];
     }
     const float v0 = vv[0], v1 = vv[1], v2 = vv[2];
+    if (sX && pnext >= 0) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) cp_async4(sX + d * stride, a.in.x + (size_t)d * cap + pnext);
+    }
     // C = D^-1 sum N v (x_I - x_p)^T = 4/dx^2 * dx * B  (Eq. 9); x += dt v (Eq. 4)
     const float c4 = 4.0f * fn;
 #pragma unroll
@@ -899,13 +917,18 @@ __device__ __forceinline__ unsigned g2p_particle(const StepArgs& a, const SceneD
     float Fn[9];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const float F0 = a.in.F[(size_t)c * cap + p], F1 = a.in.F[(size_t)(3 + c) * cap + p],
-                    F2 = a.in.F[(size_t)(6 + c) * cap + p];
+        const float F0 = sF ? sF[c * stride] : a.in.F[(size_t)c * cap + p];
+        const float F1 = sF ? sF[(3 + c) * stride] : a.in.F[(size_t)(3 + c) * cap + p];
+        const float F2 = sF ? sF[(6 + c) * stride] : a.in.F[(size_t)(6 + c) * cap + p];
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
             const float Fr = r == 0 ? F0 : (r == 1 ? F1 : F2);
             Fn[3 * r + c] = Fr + dt * (o.C[3 * r] * F0 + o.C[3 * r + 1] * F1 + o.C[3 * r + 2] * F2);
         }
+    }
+    if (sF && pnext >= 0) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) cp_async4(sF + q * stride, a.in.F + (size_t)q * cap + pnext);
     }
     ebits |= constitutive(a.model, a.plasticity, a.yield_stress, mu, lam, Fn, o.t6);
 #pragma unroll
@@ -933,6 +956,8 @@ __device__ __forceinline__ void linearize_window(const float4* vw, float4* lin)
 template <int BLOCK, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_g2p(StepArgs a)
 {
+    // x and F of each thread's next particle, copied by cp.async one particle ahead
+    __shared__ float sX[3 * BLOCK], sF[9 * BLOCK];
     __shared__ __align__(128) float4 vw[2][8 * 64];
     __shared__ __align__(16) float4 lin[kWinNodes];
     __shared__ __align__(8) unsigned long long bar[2];
@@ -951,6 +976,15 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_g2p(StepArgs a)
         const SceneDev sc = a.scenes[scene];
         const int nb = sc.nb, lb = a.sb.act_brick[item] - sc.brick_base;
         const int ox = (lb / (nb * nb)) * 4, oy = ((lb / nb) % nb) * 4, oz = (lb % nb) * 4;
+        // the brick's first particle of each thread: its copies start here (the
+        // thread's last call of the previous brick has read both buffers)
+        int pcur = tid < count ? a.sb.perm[start + tid] : -1;
+        if (pcur >= 0) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) cp_async4(&sX[d * BLOCK + tid], a.in.x + (size_t)d * a.cap + pcur);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) cp_async4(&sF[q * BLOCK + tid], a.in.F + (size_t)q * a.cap + pcur);
+        }
         linearize_window<BLOCK>(vw[buf], lin);
         __syncthreads();
         unsigned ebits = 0;
@@ -960,7 +994,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_g2p(StepArgs a)
             int key = 0;
             if (valid) {
                 G2POut o;
-                ebits |= g2p_particle(a, sc, lin, a.sb.perm[start + k], start + k, ox, oy, oz, o);
+                const int pnext = k + BLOCK < count ? a.sb.perm[start + k + BLOCK] : -1;
+                ebits |= g2p_particle(a, sc, lin, pcur, start + k, ox, oy, oz, o, &sX[tid], &sF[tid], BLOCK, pnext);
+                pcur = pnext;
 #pragma unroll
                 for (int q = 0; q < 6; ++q) a.out.tau[(size_t)q * a.cap + start + k] = o.t6[q];
                 unsigned ood = 0;
