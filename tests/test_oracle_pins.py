@@ -526,3 +526,100 @@ def test_sort_key_closed_form_on_safe_points():
     nb = n // 4
     b = (cells - 1) // 4
     assert np.array_equal(key, (b[:, 0] * nb + b[:, 1]) * nb + b[:, 2])
+
+
+# ----------------------------------------------- plasticity inside the step
+
+def _project_diagonal(eps, mu, ty):
+    """Von Mises return map of a diagonal Hencky strain (the closed form of the
+    reading used for plasticity): the deviator is scaled back to 2 mu |dev| = ty."""
+    dev = eps - eps.mean()
+    nrm = np.linalg.norm(dev)
+    gamma = nrm - ty / (2 * mu)
+    return eps - gamma * dev / nrm if gamma > 0 else eps
+
+
+@pytest.mark.parametrize("model", ["fixed_corotated", "neo_hookean"])
+def test_plasticity_inside_step_uses_mu(model):
+    # A whole substep with dt = 0, v = 0, C = 0 and no gravity moves no momentum
+    # (Eq. 8 has no term left), so every node velocity is 0 and G2P leaves x, v,
+    # C and F as they were, up to the plastic projection of F.  From a yielded
+    # F = diag(exp(e)), tr e = 0, the step must return the diagonal closed form
+    # with the particle's shear modulus: yield / (2 mu), not yield / (2 lambda).
+    n, N = 32, 50
+    mu, lam, ty = 10.0, 25.0, 2.0
+    cfg = oracle.make_config(n, 1.0, 1e-5, model=model, plasticity=True, yield_stress=ty,
+                             gravity=(0.0, 0.0, 0.0))
+    e = np.array([0.3, -0.1, -0.2])
+    st = oracle.State(_cloud(N, n, 0.4, 0.6), F=np.tile(np.diag(np.exp(e)), (N, 1, 1)), mu=mu, lam=lam)
+    x0 = st.x.copy()
+    assert oracle.run(cfg, st, 0.0, 1) == 0
+    expect = np.diag(np.exp(_project_diagonal(e, mu, ty)))
+    assert np.max(np.abs(st.F - expect)) < 1e-13
+    assert np.max(np.abs(np.diag(np.exp(_project_diagonal(e, lam, ty))) - expect)) > 1e-2  # lambda would show
+    assert np.array_equal(st.x, x0) and not st.v.any() and not st.C.any()
+
+
+def test_plasticity_projects_the_updated_F():
+    # V0 = 0 removes the stress force and g = 0, so the APIC transfers reproduce
+    # the affine field v = a + A x, C = A exactly (Eq. 8, 9).  G2P then updates
+    # F <- (I + dt C) F (Eq. 10) and projects that F.  With A and F diagonal the
+    # whole step has a closed form; projecting before the update gives another F.
+    n, N, dt = 32, 60, 1e-2
+    mu, lam, ty = 10.0, 25.0, 2.0
+    cfg = oracle.make_config(n, 1.0, 0.0, plasticity=True, yield_stress=ty, gravity=(0.0, 0.0, 0.0))
+    a, Ad = np.array([0.1, -0.2, 0.05]), np.array([2.0, -3.0, 1.5])
+    A = np.diag(Ad)
+    e0 = np.array([0.3, -0.1, -0.2])
+    x = _cloud(N, n, 0.45, 0.55)
+    v = a + x @ A.T
+    st = oracle.State(x, v, np.tile(A, (N, 1, 1)), np.tile(np.diag(np.exp(e0)), (N, 1, 1)), mu=mu, lam=lam)
+    assert oracle.run(cfg, st, dt, 1) == 0
+    expect = np.diag(np.exp(_project_diagonal(np.log(1 + dt * Ad) + e0, mu, ty)))
+    assert np.max(np.abs(st.F - expect)) < 1e-10
+    assert np.max(np.abs(st.v - v)) < 1e-12 and np.max(np.abs(st.C - A)) < 1e-10
+    assert np.max(np.abs(st.x - (x + dt * v))) < 1e-13
+    wrong_order = np.diag((1 + dt * Ad) * np.exp(_project_diagonal(e0, mu, ty)))
+    assert np.max(np.abs(wrong_order - expect)) > 1e-3
+
+
+# ------------------------------------------------------------------- loss
+
+def test_loss_hand_worked():
+    # Loss of the differentiable workload: squared distance of the particle
+    # centroid to the target plus the mean squared particle speed, worked by
+    # hand in binary fractions (tests/golden/loss_hand_worked.txt).
+    parts, target, expect = [], None, None
+    for line in open(os.path.join(GOLDEN, "loss_hand_worked.txt")):
+        f = line.split()
+        if not f or f[0].startswith("#"):
+            continue
+        if f[0] == "particle":
+            parts.append([float(t) for t in f[1:]])
+        elif f[0] == "target":
+            target = [float(t) for t in f[1:]]
+        elif f[0] == "loss":
+            expect = float(f[1])
+    parts = np.array(parts)
+    assert oracle.loss(parts[:, :3], parts[:, 3:], target) == expect
+
+
+# ------------------------------------------------------ paper's timing scene
+
+def test_paper_timing_scene_constants():
+    # Sec. III-D: 0.02 s per step, 10 substeps of dt = 0.002, 175,616 grid nodes
+    # (tests/golden/paper_constants.txt); the workload of that scene uses them,
+    # and its explicit step stays inside the CFL limit.
+    kv = {}
+    for line in open(os.path.join(GOLDEN, "paper_constants.txt")):
+        f = line.split()
+        if f and not f[0].startswith("#"):
+            kv[f[0]] = float(f[1])
+    sc = W.paper_timing_cube(N=4096, steps=1)
+    assert sc["n"] ** 3 == kv["grid_nodes"] and sc["n"] == kv["grid_side"]
+    assert sc["dt"] == kv["substep_dt"]
+    assert sc["substeps"] == kv["substeps_per_step"]
+    assert abs(sc["substeps"] * sc["dt"] - kv["step_seconds"]) < 1e-15
+    mu, lam = oracle.lame(float(sc["E"][0]), float(sc["nu"][0]))
+    c = math.sqrt((lam + 2 * mu) / sc["rho"])
+    assert sc["dt"] * c * sc["n"] <= 0.3
