@@ -89,7 +89,8 @@ enum {
     MPM_OPT_G2P_THREADS = 4,    /* threads per CTA of the G2P kernel: 128 (default) /
                                    256 / 512                                        */
     MPM_OPT_CTAS_PER_SM = 5,    /* persistent CTAs per SM for P2G/G2P (0 = occupancy max) */
-    MPM_OPT_GRAPH_CHUNK = 6,    /* substeps captured per graph (1..64)              */
+    MPM_OPT_GRAPH_CHUNK = 6,    /* most substeps captured per graph (1..64, default 32):
+                                   a call of k substeps replays ceil(k/chunk) graphs */
     MPM_OPT_PHASE_TIMING = 7,   /* 0/1: record CUDA events around each phase of every
                                    substep (forces direct launches); see mpm_phase_stats */
     MPM_OPT_P2G_CHUNK = 8,      /* particles staged per pass of the P2G kernel: 384,
@@ -153,7 +154,9 @@ typedef struct mpm_ctx mpm_ctx; /* opaque; owned by the library */
 
 /* ---- lifecycle ------------------------------------------------------- */
 
-/* Create a context on the current CUDA device; `cuda_stream` is a cudaStream_t
+/* Create a context on the current CUDA device: the scene container of the
+ * paper's object model (Sec. V-A, V-B: a Scene created by the SimulationFactory,
+ * here holding n_scenes independent scenes).  `cuda_stream` is a cudaStream_t
  * on which all of the context's work is ordered (NULL: the context creates and
  * owns a non-blocking stream, since substeps are replayed from CUDA graphs,
  * which cannot be captured on the legacy default stream).  Allocates every device buffer the substep needs for

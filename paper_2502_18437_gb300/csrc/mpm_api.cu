@@ -652,7 +652,11 @@ extern "C" int mpm_substep(mpm_ctx* c, float dt, int n_substeps)
     }
     int left = n_substeps;
     const bool pending = c->fused && c->g_pending && c->g_dt == dt;
-    if (!pending) {
+    // One direct substep first where the captured graphs' assumptions do not hold
+    // yet: the fused kernel needs this state's P2G already in G, and the captured
+    // P2G reads the stress that the previous G2P stored.
+    const bool direct_first = c->fused ? !pending : (!c->tau_valid || c->g_dirty);
+    if (direct_first) {
         // a fresh P2G: clear whatever scatter G still holds, then one direct substep
         if (c->g_dirty) MPM_CK(cudaMemsetAsync(c->G, 0, sizeof(float4) * (size_t)c->total_bricks * 64, c->stream));
         if ((st = enqueue_substep(c, dt, c->st[c->cur], c->st[c->cur ^ 1], true))) return st;
@@ -672,7 +676,7 @@ extern "C" int mpm_substep(mpm_ctx* c, float dt, int n_substeps)
         return MPM_OK;
     }
     while (left > 0) {
-        const int L = left >= c->graph_chunk ? c->graph_chunk : 1;
+        const int L = left < c->graph_chunk ? left : c->graph_chunk;
         auto key = std::make_tuple(float_bits(dt), L, c->cur);
         auto it = c->graphs.find(key);
         if (it == c->graphs.end()) {

@@ -61,7 +61,7 @@ struct mpm_ctx {
     int g2p_threads = 128;
     int g2p_regs64 = 1;
     int ctas_per_sm = 0;
-    int graph_chunk = 16;
+    int graph_chunk = 32;
     int phase_timing = 0;
     int fused = 0;
     // occupancy (resident CTAs per SM) of each kernel variant on this device, 0 = not asked yet

@@ -44,14 +44,37 @@ def test_source_digest_changes_with_any_kernel_source(tmp_path, monkeypatch):
 
 
 def test_algorithmic_bytes_per_unit():
+    # The method's bytes per particle-substep: P2G reads x, v, C, F (96 B), G2P
+    # reads x, F and writes x, v, C, F (144 B), the sort writes and reads key and
+    # permutation (16 B); the grid moves 72 B per active node.
+    N, nodes = 1 << 20, 3150 * 64
+    ab = bench.algorithmic_bytes(N, nodes)
+    assert ab == {"sort": 16 * N, "p2g": 96 * N, "grid": 72 * nodes, "g2p": 144 * N}
+    assert (sum(ab.values()) / N) == pytest.approx(256 + 72 * nodes / N)
+    # ~270 B per particle-substep at 8 particles per cell and ~1.5 active nodes per cell
+    assert 265 < 256 + 72 * (1.5 / 8) < 271
+
+
+def test_implementation_bytes_per_unit():
     N, bricks, nodes = 1 << 20, 64 ** 3, 3150 * 64
-    ab = bench.algorithmic_bytes(N, bricks, nodes)
-    assert ab["sort"] == 8 * bricks + 17 * N
-    assert ab["p2g"] == 93 * N + 16 * nodes
-    assert ab["grid"] == 48 * nodes
-    assert ab["g2p"] == 188 * N + 16 * nodes
+    ib = bench.implementation_bytes(N, bricks, nodes)
+    assert ib["sort"] == 8 * bricks + 17 * N
+    assert ib["p2g"] == 93 * N + 16 * nodes
+    assert ib["grid"] == 48 * nodes
+    assert ib["g2p"] == 188 * N + 16 * nodes
     # per-particle materials add mu and lambda to G2P's reads and writes
-    assert bench.algorithmic_bytes(N, bricks, nodes, pp_mat=True)["g2p"] == ab["g2p"] + 16 * N
+    assert bench.implementation_bytes(N, bricks, nodes, pp_mat=True)["g2p"] == ib["g2p"] + 16 * N
+
+
+def test_roofline_fraction_reproduces_from_the_survey_bytes():
+    # frac = algorithmic bytes of the dominant kernel x N / its launch time / peak
+    N, nodes = 1 << 20, 201600
+    per = {"sort": 0.017, "p2g": 0.069, "grid": 0.011, "g2p": 0.0805}
+    r = bench.roofline_fields(N, 64 ** 3, nodes, per, 0.162, 6790.7, "measured")
+    assert r["kernel"] == "g2p"
+    assert r["frac"] == pytest.approx(144 * N / (0.0805e-3) / 1e9 / 6790.7, abs=1e-4)
+    assert r["whole_substep_frac"] == pytest.approx((256 * N + 72 * nodes) / 0.162e-3 / 1e9 / 6790.7, abs=1e-4)
+    assert r["implementation_bytes_per_launch"] == 188 * N + 16 * nodes
 
 
 @pytest.mark.parametrize("world,units,ms", [(1, 1000, 10.0), (4, 2500, 8.0)])

@@ -207,3 +207,77 @@ def test_rigid_motion_follows_set_velocity():
         imp = sim.impulse(0)
     assert st["v"][:, 1].max() > 0.2
     assert imp[0, 1] < 0  # the soft body pushes back on the rigid
+
+
+def test_bounded_wait_times_out_on_a_host_stall():
+    # A host function enqueued on the context's stream blocks it for longer than
+    # the context's timeout (only the host waits; no GPU work stalls).  The
+    # blocking read must give up with TIMEOUT instead of waiting it out, and the
+    # next read succeeds once the stream has drained.
+    import ctypes
+    import threading
+    import time
+
+    torch = pytest.importorskip("torch")
+    cuda = ctypes.CDLL("libcuda.so.1")
+    hostfn_t = ctypes.CFUNCTYPE(None, ctypes.c_void_p)
+    release = threading.Event()
+    cb = hostfn_t(lambda _: release.wait(10.0))  # bounded even if the test failed to release it
+    cuda.cuLaunchHostFunc.argtypes = [ctypes.c_void_p, hostfn_t, ctypes.c_void_p]
+    cuda.cuLaunchHostFunc.restype = ctypes.c_int
+    stream = torch.cuda.Stream()
+    sc = small_cube(4)
+    with mpm.from_workload(sc, stream=stream.cuda_stream, timeout_ms=200) as sim:
+        sim.substep(1e-4, 2)
+        assert cuda.cuLaunchHostFunc(stream.cuda_stream, cb, None) == 0
+        try:
+            t0 = time.perf_counter()
+            out = sim.read_state(0, ("x",), check=False)
+            waited = time.perf_counter() - t0
+            assert out["status"] == -8, mpm.STATUS.get(out["status"])
+            assert 0.15 < waited < 3.0, waited
+            with pytest.raises(mpm.MPMError) as e:
+                sim.error_bits(0)
+            assert e.value.status == -8
+        finally:
+            release.set()
+        stream.synchronize()
+        out = sim.read_state(0, ("x", "v"))
+        assert np.all(np.isfinite(out["x"])) and sim.error_bits(0) == 0
+
+
+def test_batched_slicers_match_oracle_per_scene():
+    # Scenes of the batched workload (ragged counts, 32^3 and 64^3 grids, one
+    # yawed QuadSlicer each), with every blade lowered into its block so that
+    # its faces and edge touch tissue: one substep from perturbed
+    # states in one batched launch per phase, every scene against the oracle run
+    # on that scene alone, the blades' impulses included.
+    from tests.parity_util import Scales, oracle_rigids, perturbed
+
+    scenes = W.batched_scenes(n_scenes=8, substeps=1)
+    for sc in scenes:
+        b = sc["rigids"][0]
+        top = float(sc["x"][:, 1].max())
+        b["center"] = (b["center"][0], top - 0.02 + b["half"][1], b["center"][2])
+    pert = [perturbed(sc, seed=100 + s, f_amp=0.02, c_amp=2.0) for s, sc in enumerate(scenes)]
+    with mpm.from_scenes(scenes) as sim:
+        for s, p in enumerate(pert):
+            sim.write_state(s, v=p[0], C=p[1], F=p[2])
+        for s in range(len(scenes)):
+            sim.impulse(s)
+        sim.substep(1e-4, 1)
+        got = [sim.read_state(s, ("x", "v", "C", "F", "impulse")) for s in range(len(scenes))]
+    touched = 0
+    for s, sc in enumerate(scenes):
+        st = oracle_state(sc, sc["x"], *pert[s])
+        rig, nr = oracle_rigids(sc)
+        assert oracle.substep(oracle_cfg(sc), st, 1e-4, rig, nr)[2] == 0
+        err = Scales(sc, pert[s][2], 1e-4)
+        for f in ("x", "F"):
+            assert_close(f"scene {s} {f}", got[s][f], getattr(st, f))
+        assert_close(f"scene {s} v", got[s]["v"], st.v, atol_floor=err.atol_v(st.v))
+        assert_close(f"scene {s} C", got[s]["C"], st.C, atol_floor=err.atol_C(st.v))
+        imp = oracle.rigid_impulse(rig[0])
+        assert_close(f"scene {s} impulse", got[s]["impulse"][0], imp, rtol=1e-4, rel_scale=1e-4)
+        touched += np.abs(imp[:3]).max() > 0
+    assert touched == len(scenes)

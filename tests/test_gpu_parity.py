@@ -220,3 +220,25 @@ def test_degenerate_F_fixed_corotated():
     st, gm, gv, err, _ = oracle_one_step(sc, x, v, C, F)
     assert err == 0
     check_fields(sc, out, st, Scales(sc, F))
+
+
+@pytest.mark.parametrize("steps_before", [0, 15])
+def test_box_contact_matches_oracle(steps_before):
+    # A rotated box (Sec. IV-A, solid SDF, Eq. 11 friction) pressed down into a
+    # soft cube while turning: inside-face, edge and corner normals all occur.
+    # One substep from the same state at two points of the trajectory, the
+    # box's impulse included.
+    sc = W.elastic_cube(n=32, n_side=14, corner=(0.32, 0.1, 0.33), substeps=40)
+    q = np.array([0.96, 0.12, 0.2, -0.15])
+    q /= np.linalg.norm(q)
+    sc["rigids"] = [W.box((0.43 + 0.21 / 32, 0.37 - 0.37 / 32, 0.43 - 0.13 / 32), (0.1, 0.06, 0.08),
+                          quat=tuple(q), vel=(0.02, -0.3, 0.0), omega=(0.0, 1.5, 0.5), mu_k=0.4, c_d=0.9,
+                          margin=0.5 / 32)]
+    v, C, F = perturbed(sc, seed=21, f_amp=0.01, c_amp=1.0)
+    x, v, C, F, out = gpu_one_step(sc, v, C, F, steps_before=steps_before)
+    st, gm, gv, err, imp = oracle_one_step(sc, x, v, C, F, steps_before)
+    assert err == 0
+    check_fields(sc, out, st, Scales(sc, F))
+    check_grid(sc, out, gm, gv, Scales(sc, F))
+    assert np.abs(imp[0, :3]).max() > 0  # in contact
+    assert_close("box impulse", out["impulse"][0], imp[0], rtol=1e-4, rel_scale=1e-4)
