@@ -78,6 +78,8 @@ def lib():
         L.orc_geometry.restype = ct.c_int
         L.orc_geometry.argtypes = [ct.POINTER(Rigid), D, D, D, D]
         L.orc_contact_node.argtypes = [ct.POINTER(Rigid), D, ct.c_double, D]
+        L.orc_push_out.restype = ct.c_int
+        L.orc_push_out.argtypes = [ct.POINTER(Rigid), D]
         L.orc_p2g.restype = ct.c_int
         L.orc_p2g.argtypes = [ct.POINTER(Config), ct.c_int, D, D, D, D, D, D, ct.c_double, D, D]
         L.orc_grid_update.restype = ct.c_int
@@ -233,6 +235,13 @@ def contact_node(rigid, x, m, v):
     v = _arr(v, (3,)).copy()
     lib().orc_contact_node(ct.byref(rigid), _dp(x), float(m), _dp(v))
     return v
+
+
+def push_out(rigid, x):
+    """(x after the push-out against one rigid, whether it moved)."""
+    x = _arr(x, (3,)).copy()
+    moved = lib().orc_push_out(ct.byref(rigid), _dp(x))
+    return x, bool(moved)
 
 
 def rigid_advance(rigid, dt):

@@ -13,7 +13,8 @@
  *                   Eq. 12) and domain boundaries
  *   particle loop : affine transfer (Eq. 9), advection (Eq. 4), deformation
  *                   gradient (Eq. 10), constitutive update
- *   reset grid.
+ *   reset grid; rigid poses advance; particles left inside solid rigids are
+ *   pushed out to the surface (Sec. IV-A).
  * Passages the paper leaves open are resolved by the reading written at the
  * function that needs it.  No blocking, fusion or reordering is done beyond the
  * order of Algorithm 1.
@@ -475,6 +476,26 @@ void orc_contact_node(orc_rigid* r, const double xI[3], double mI, double v[3])
     for (int i = 0; i < 3; ++i) r->impulse[3 + i] -= ang[i];
 }
 
+/* Particle push-out (Sec. IV-A): after the grid-level contact, particles that
+ * still ended the substep inside a rigid are pushed out of it, after the
+ * particle collision step of Stomakhin et al. 2013.  Reading: this applies to
+ * the solid shapes (sphere, box), evaluated at the rigid's pose at the end of
+ * the substep; a particle with sdf(x) < 0 is moved to the nearest surface
+ * point, x <- x - sdf(x) n(x) with n the outward SDF gradient, in rigid-id
+ * order; its velocity, C and F stay as the transfers made them, and no
+ * momentum is booked to the rigid.  Blades and line segments push nothing
+ * out: the tissue is meant to close around them (Sec. IV-B, IV-C).
+ * Returns 1 when x moved. */
+int orc_push_out(const orc_rigid* r, double x[3])
+{
+    if (r->type != ORC_SPHERE && r->type != ORC_BOX) return 0;
+    double n[3], t[3], dist;
+    int code = orc_geometry(r, x, n, t, &dist);
+    if (code == ORC_REGION_NONE || !(dist < 0.0)) return 0;
+    for (int i = 0; i < 3; ++i) x[i] -= dist * n[i];
+    return 1;
+}
+
 /* ------------------------------------------------------------ the step */
 
 static int base_and_frac(const orc_config* cfg, const double xp[3], int b[3], double f[3])
@@ -602,8 +623,9 @@ int orc_g2p(const orc_config* cfg, int N, double* x, double* v, double* C, doubl
     return err;
 }
 
-/* One full substep (Algorithm 1): P2G, grid update, G2P, reset grid, and the
- * kinematic advance of the rigids.  grid: caller-provided scratch of n^3 x 4
+/* One full substep (Algorithm 1): P2G, grid update, G2P, reset grid, the
+ * kinematic advance of the rigids, and the push-out of particles left inside
+ * solid rigids.  grid: caller-provided scratch of n^3 x 4
  * doubles (mass + 3 momentum/velocity); on return it holds the node masses in
  * [0, n^3) and node velocities after the grid update in [n^3, 4 n^3) (the
  * reset of Algorithm 1 happens at the start of the next call). */
@@ -620,6 +642,8 @@ int orc_substep(const orc_config* cfg, int N, double* x, double* v, double* C, d
     err |= orc_grid_update(cfg, gm, gmv, n_rigid, rigids, dt);
     err |= orc_g2p(cfg, N, x, v, C, F, mu, dt, gmv);
     for (int r = 0; r < n_rigid; ++r) orc_rigid_advance(&rigids[r], dt);
+    for (int p = 0; p < N; ++p)
+        for (int r = 0; r < n_rigid; ++r) orc_push_out(&rigids[r], x + 3 * p);
     return err;
 }
 

@@ -623,3 +623,75 @@ def test_paper_timing_scene_constants():
     mu, lam = oracle.lame(float(sc["E"][0]), float(sc["nu"][0]))
     c = math.sqrt((lam + 2 * mu) / sc["rho"])
     assert sc["dt"] * c * sc["n"] <= 0.3
+
+
+# ----------------------------------------------------------- push-out
+
+def test_push_out_sphere_closed_form():
+    # Sec. IV-A particle correction: a point inside a sphere goes to the surface
+    # point on the ray from the centre, c + R (x - c)/|x - c|; outside points stay.
+    c, R = np.array([0.4, 0.5, 0.6]), 0.1
+    r = oracle.make_rigid(W.sphere(tuple(c), R))
+    g = np.random.default_rng(31)
+    for _ in range(100):
+        d = g.normal(size=3)
+        d /= np.linalg.norm(d)
+        rad = g.uniform(0.01, 0.2)
+        x0 = c + rad * d
+        x1, moved = oracle.push_out(r, x0)
+        if rad < R:
+            assert moved and np.max(np.abs(x1 - (c + R * d))) < 1e-15
+        else:
+            assert not moved and np.array_equal(x1, x0)
+
+
+def test_push_out_box_nearest_face():
+    # Inside a (rotated) box the nearest face is the one of largest q = |p| - h;
+    # the point lands on that face: its body coordinate along the face normal
+    # becomes +-h, the other two body coordinates are kept.
+    q = np.array([0.9, 0.2, -0.3, 0.25])
+    q /= np.linalg.norm(q)
+    half = np.array([0.08, 0.05, 0.12])
+    r = oracle.make_rigid(W.box((0.5, 0.45, 0.55), tuple(half), quat=tuple(q)))
+    c, Rm = oracle.rigid_pose(r)
+    g = np.random.default_rng(32)
+    for _ in range(200):
+        p = g.uniform(-1.3, 1.3, 3) * half
+        x1, moved = oracle.push_out(r, c + Rm @ p)
+        inside = np.all(np.abs(p) < half)
+        assert moved == inside
+        if inside:
+            ax = int(np.argmax(np.abs(p) - half))
+            p1 = Rm.T @ (x1 - c)
+            expect = p.copy()
+            expect[ax] = np.sign(p[ax]) * half[ax]
+            assert np.max(np.abs(p1 - expect)) < 1e-13
+
+
+def test_push_out_leaves_blades_and_segments():
+    # Blades and line segments are crossed by the tissue by design (Sec. IV-B, IV-C).
+    blade = oracle.make_rigid(W.quad_slicer((0.5, 0.5, 0.5), (1, 0, 0, 0), half_edge=0.1, half_depth=0.05,
+                                            thickness=0.01))
+    seg = oracle.make_rigid(W.segments((0.5, 0.5, 0.5), (1, 0, 0, 0), [[-0.1, 0, 0], [0.1, 0, 0]], radius=0.02))
+    for r in (blade, seg):
+        x1, moved = oracle.push_out(r, np.array([0.5, 0.5, 0.5]))
+        assert not moved and np.array_equal(x1, [0.5, 0.5, 0.5])
+
+
+def test_push_out_in_the_step_uses_the_moved_pose():
+    # Particles resting inside a sphere that moves by dt * vel during the
+    # substep end on the sphere's surface at its new centre (G2P, then the
+    # kinematic advance, then the push-out); no node momentum changes for it.
+    n, dt = 32, 1e-3
+    cfg = oracle.make_config(n, 1.0, 1e-6, gravity=(0.0, 0.0, 0.0))
+    c0, R, vel = np.array([0.5, 0.5, 0.5]), 0.08, np.array([0.3, -0.2, 0.1])
+    rig = oracle.rigid_array([W.sphere(tuple(c0), R, vel=tuple(vel), mu_k=0.0, margin=0.0)])
+    g = np.random.default_rng(33)
+    d = g.normal(size=(40, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    x = c0 + d * g.uniform(0.02, 0.07, (40, 1))
+    st = oracle.State(x, mu=0.0, lam=0.0)
+    oracle.substep(cfg, st, dt, rig, 1)
+    c1 = c0 + dt * vel
+    assert np.max(np.abs(oracle.rigid_pose(rig[0])[0] - c1)) < 1e-15
+    assert np.max(np.abs(np.linalg.norm(st.x - c1, axis=1) - R)) < 1e-13
