@@ -270,6 +270,21 @@ int mpm_tape_begin(mpm_ctx* ctx);
 int mpm_backward(mpm_ctx* ctx, const float* dL_dx, const float* dL_dv, float* dL_dE,
                  float* dL_dnu, float* dL_dv0, int mem);
 
+/* Reverse-mode gradient with respect to the whole particle state at
+ * mpm_tape_begin, for losses of any field of the final state (the same
+ * hand-written adjoint kernels and tape as mpm_backward).  bar_in[0..3]: the
+ * adjoints dL/dx (N,3), dL/dv (N,3), dL/dC (N,3,3), dL/dF (N,3,3) of the final
+ * state over ALL particles of the context, scene-major id order; a NULL array
+ * or a NULL entry is zero.  bar_out[0..3] (NULL array or entries = not wanted):
+ * dL/dx0, dL/dv0, dL/dC0, dL/dF0 of the state at mpm_tape_begin, same layout;
+ * dL_dmu, dL_dlam (N, may be NULL): gradients with respect to the per-particle
+ * Lame parameters.  The sort is piecewise constant in x and contributes no
+ * derivative; the rest follows mpm_backward (no rigid in any scene, no
+ * plasticity).  Blocks until done (bounded).
+ * Errors: INVALID_ARGUMENT, STATE, TIMEOUT, CUDA. */
+int mpm_backward_state(mpm_ctx* ctx, const float* const* bar_in, float* const* bar_out, float* dL_dmu,
+                       float* dL_dlam, int mem);
+
 /* ---- batching -------------------------------------------------------- */
 
 /* Time candidate launch shapes (P2G chunk, threads per CTA and register
@@ -302,8 +317,9 @@ int mpm_autotune(mpm_ctx* ctx, float dt, int trial_substeps, float* best_ms_out)
  * It allocates nothing: its scratch is one static device array of
  * 10,486,784 bytes that every device loading the library reserves until the
  * process exits.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress) with the device current; make that first
- * call before any stream capture.  All calls share the array, so calls that
+ * address (cudaGetSymbolAddress) with the device current, and looks it up
+ * again after that device's context was reset and recreated; make that first
+ * call (and the first after a reset) before any stream capture.  All calls share the array, so calls that
  * overlap on the GPU race and must be serialised by the caller.
  * Errors: INVALID_ARGUMENT (n not a multiple of 4 or < 8, N < 0, NULL
  * buffers), CAPACITY (N > MPM_NOALLOC_MAX_PARTICLES or n > MPM_NOALLOC_MAX_GRID),

@@ -47,7 +47,7 @@ struct mpm_tape {
     int* perms = nullptr;      // [max_steps][cap] recorded permutations
     float* adj = nullptr;      // 2 adjoint states, [2][24][cap]
     float* gmat = nullptr;     // [2][cap] mu, lambda gradients (global particle order)
-    float* io = nullptr;       // [9][cap] staged gradient inputs / outputs
+    float* io = nullptr;       // [28][cap] staged gradient inputs / outputs
 };
 
 namespace mpm {
@@ -219,22 +219,25 @@ __device__ void stress_and_vjp(int model, const float F[9], float mu, float lam,
 
 // ------------------------------------------------------------------ seed
 
-__global__ void k_adj_seed(StepArgs a, PState st, const float* dLdx, const float* dLdv, AdjState nxt)
+// Adjoint of the final state, from caller buffers in scene-major id order
+// (bar[0..3] = x, v, C, F; a NULL buffer is zero) to storage order.
+struct SeedIn {
+    const float* bar[4];
+};
+
+__global__ void k_adj_seed(StepArgs a, PState st, SeedIn in, AdjState nxt)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= a.r.np) return;
     const int i = a.r.p0 + g;
     const size_t cap = a.cap;
     const int gid = a.scenes[scene_of(a, i)].p_begin + st.id[i];
+    float* dst[4] = {nxt.x, nxt.v, nxt.C, nxt.F};
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        nxt.x[d * cap + i] = dLdx ? dLdx[3 * (size_t)gid + d] : 0.f;
-        nxt.v[d * cap + i] = dLdv ? dLdv[3 * (size_t)gid + d] : 0.f;
-    }
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
-        nxt.C[q * cap + i] = 0.f;
-        nxt.F[q * cap + i] = 0.f;
+    for (int f = 0; f < 4; ++f) {
+        const int comps = f < 2 ? 3 : 9;
+        const float* src = in.bar[f];
+        for (int d = 0; d < comps; ++d) dst[f][d * cap + i] = src ? src[comps * (size_t)gid + d] : 0.f;
     }
 }
 
@@ -251,7 +254,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_g2p_adj(AdjArgs q)
     const size_t cap = a.cap;
     const int n_act = a.sb.counters[CTR_N_ACT];
     int* work = &a.sb.counters[CTR_WORK_G2P];
-    walker_init<kAdjThreads>(a, n_act, vw, bar, s_item, work, false);
+    walker_init<kAdjThreads>(a, n_act, vw, bar, s_item, work);
     unsigned phase[2] = {0u, 0u};
     int buf = 0;
     for (;;) {
@@ -425,7 +428,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_p2g_adj(AdjArgs q)
     const size_t cap = a.cap;
     const int n_act = a.sb.counters[CTR_N_ACT];
     int* work = &a.sb.counters[CTR_WORK_P2G];
-    walker_init<kAdjThreads>(a, n_act, vw, bar, s_item, work, false);
+    walker_init<kAdjThreads>(a, n_act, vw, bar, s_item, work);
     unsigned phase[2] = {0u, 0u};
     int buf = 0;
     for (;;) {
@@ -518,10 +521,16 @@ __global__ void __launch_bounds__(kAdjThreads) k_p2g_adj(AdjArgs q)
 }
 
 // ---------------------------------------------------------------- output
-// Gradients w.r.t. the initial velocities and the per-particle Young's
-// modulus and Poisson ratio (mu = E / (2(1+nu)), lambda = E nu / ((1+nu)(1-2nu))).
-__global__ void k_adj_out(StepArgs a, PState st0, AdjState adj0, const float* gmu, const float* glam, float* dE,
-                          float* dnu, float* dv0)
+// Outputs in scene-major id order: the adjoint of the state at mpm_tape_begin
+// (out[0..3] = x, v, C, F; NULL = not wanted) and the gradients with respect to
+// the per-particle Young's modulus and Poisson ratio (mu = E / (2(1+nu)),
+// lambda = E nu / ((1+nu)(1-2nu))) and Lame parameters.
+struct AdjOut {
+    float* bar[4];
+    float *dE, *dnu, *dmu, *dlam;
+};
+
+__global__ void k_adj_out(StepArgs a, PState st0, AdjState adj0, const float* gmu, const float* glam, AdjOut o)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= a.r.np) return;
@@ -529,17 +538,23 @@ __global__ void k_adj_out(StepArgs a, PState st0, AdjState adj0, const float* gm
     const size_t cap = a.cap;
     const SceneDev sc = a.scenes[scene_of(a, i)];
     const int gid = sc.p_begin + st0.id[i];
-    if (dv0)
+    const float* src[4] = {adj0.x, adj0.v, adj0.C, adj0.F};
 #pragma unroll
-        for (int d = 0; d < 3; ++d) dv0[3 * (size_t)gid + d] = adj0.v[d * cap + i];
+    for (int f = 0; f < 4; ++f) {
+        if (!o.bar[f]) continue;
+        const int comps = f < 2 ? 3 : 9;
+        for (int d = 0; d < comps; ++d) o.bar[f][comps * (size_t)gid + d] = src[f][d * cap + i];
+    }
     const float mu = sc.pp_mat ? st0.mu[i] : sc.mu, lam = sc.pp_mat ? st0.lam[i] : sc.lam;
     const float E = mu * (3.f * lam + 2.f * mu) / (lam + mu);
     const float nu = lam / (2.f * (lam + mu));
     const float a1 = 1.f + nu, a2 = 1.f - 2.f * nu;
     const float dmu_dE = 1.f / (2.f * a1), dmu_dnu = -E / (2.f * a1 * a1);
     const float dlam_dE = nu / (a1 * a2), dlam_dnu = E * (1.f + 2.f * nu * nu) / (a1 * a1 * a2 * a2);
-    if (dE) dE[gid] = gmu[gid] * dmu_dE + glam[gid] * dlam_dE;
-    if (dnu) dnu[gid] = gmu[gid] * dmu_dnu + glam[gid] * dlam_dnu;
+    if (o.dE) o.dE[gid] = gmu[gid] * dmu_dE + glam[gid] * dlam_dE;
+    if (o.dnu) o.dnu[gid] = gmu[gid] * dmu_dnu + glam[gid] * dlam_dnu;
+    if (o.dmu) o.dmu[gid] = gmu[gid];
+    if (o.dlam) o.dlam[gid] = glam[gid];
 }
 
 }  // namespace mpm
@@ -553,6 +568,10 @@ __global__ void k_adj_out(StepArgs a, PState st0, AdjState adj0, const float* gm
     } while (0)
 
 static int n_blocks(long long n, int t) { return (int)((n + t - 1) / t); }
+
+// staging of host gradient buffers: 24 floats of state adjoint + dE, dnu, dmu, dlam per particle
+constexpr int kIoFloats = 28;
+static const int kComps[4] = {3, 3, 9, 9};
 
 void mpm_tape_free(mpm_ctx* c)
 {
@@ -601,7 +620,7 @@ extern "C" int mpm_tape_begin(mpm_ctx* c)
         if (e == cudaSuccess) e = cudaMalloc(&t->perms, sizeof(int) * (size_t)c->cap * t->max_steps);
         if (e == cudaSuccess) e = cudaMalloc(&t->adj, sizeof(float) * 48 * (size_t)c->cap);
         if (e == cudaSuccess) e = cudaMalloc(&t->gmat, sizeof(float) * 2 * (size_t)c->cap);
-        if (e == cudaSuccess) e = cudaMalloc(&t->io, sizeof(float) * 9 * (size_t)c->cap);
+        if (e == cudaSuccess) e = cudaMalloc(&t->io, sizeof(float) * kIoFloats * (size_t)c->cap);
         if (e != cudaSuccess) {
             mpm_tape_free(c);
             return status_from_cuda(e);
@@ -656,34 +675,16 @@ static int sort_with_perm(mpm_ctx* c, StepArgs& a, const PState& state, int* per
     return MPM_OK;
 }
 
-extern "C" int mpm_backward(mpm_ctx* c, const float* dLdx, const float* dLdv, float* dLdE, float* dLdnu,
-                            float* dLdv0, int mem)
+// Reverse of every recorded substep from the adjoint of the final state
+// (seeds, device pointers in id order or NULL) to the adjoint of the state at
+// mpm_tape_begin and the material gradients (outputs, device pointers or NULL).
+static int backward_device(mpm_ctx* c, const SeedIn& seeds, const AdjOut& outs)
 {
-    if (!c || (mem != MPM_MEM_HOST && mem != MPM_MEM_DEVICE)) return MPM_ERR_INVALID_ARGUMENT;
-    if (!c->tape || !c->recording) return MPM_ERR_STATE;
-    if (any_rigid(c)) return MPM_ERR_STATE;
     mpm_tape* t = c->tape;
     const int T = (int)t->dts.size();
     const int N = c->total_particles;
     const size_t cap = c->cap;
-    int st = upload_scenes(c);
-    if (st) return st;
-    // inputs
-    float* dx_d = nullptr;
-    float* dv_d = nullptr;
-    if (mem == MPM_MEM_HOST) {
-        if (dLdx) {
-            dx_d = t->io;
-            MPM_CKA(cudaMemcpyAsync(dx_d, dLdx, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, c->stream));
-        }
-        if (dLdv) {
-            dv_d = t->io + 3 * cap;
-            MPM_CKA(cudaMemcpyAsync(dv_d, dLdv, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, c->stream));
-        }
-    } else {
-        dx_d = const_cast<float*>(dLdx);
-        dv_d = const_cast<float*>(dLdv);
-    }
+    int st;
     // the recompute advances the scene clocks; keep them
     std::vector<double> t_save(c->n_scenes);
     std::vector<int> e_save(c->n_scenes);
@@ -698,7 +699,7 @@ extern "C" int mpm_backward(mpm_ctx* c, const float* dLdx, const float* dLdv, fl
     float* glam = t->gmat + cap;
     {
         StepArgs a = step_args(c, 0.f, 0, c->n_scenes, c->st[c->cur], c->st[c->cur]);
-        if (N > 0) k_adj_seed<<<n_blocks(N, 256), 256, 0, c->stream>>>(a, c->st[c->cur], dx_d, dv_d, adj[nxt]);
+        if (N > 0) k_adj_seed<<<n_blocks(N, 256), 256, 0, c->stream>>>(a, c->st[c->cur], seeds, adj[nxt]);
         MPM_CKA(cudaGetLastError());
     }
     const size_t sbytes = state_bytes(c->cap);
@@ -739,29 +740,71 @@ extern "C" int mpm_backward(mpm_ctx* c, const float* dLdx, const float* dLdv, fl
         }
     }
     // outputs (adj[nxt] is the adjoint of the state at mpm_tape_begin)
-    {
-        const PState st0 = state_view(t->ckpt[0], c->cap);
-        StepArgs a = step_args(c, 0.f, 0, c->n_scenes, st0, st0);
-        float* oE = dLdE;
-        float* onu = dLdnu;
-        float* ov0 = dLdv0;
-        if (mem == MPM_MEM_HOST) {
-            oE = dLdE ? t->io + 6 * cap : nullptr;
-            onu = dLdnu ? t->io + 7 * cap : nullptr;
-            ov0 = dLdv0 ? t->io : nullptr;  // inputs are consumed by now
+    const PState st0 = state_view(t->ckpt[0], c->cap);
+    StepArgs a = step_args(c, 0.f, 0, c->n_scenes, st0, st0);
+    if (N > 0) k_adj_out<<<n_blocks(N, 256), 256, 0, c->stream>>>(a, st0, adj[nxt], gmu, glam, outs);
+    MPM_CKA(cudaGetLastError());
+    MPM_CKA(cudaMemcpyAsync(c->d_time, t_save.data(), sizeof(double) * c->n_scenes, cudaMemcpyHostToDevice, c->stream));
+    MPM_CKA(cudaMemcpyAsync(c->d_epoch, e_save.data(), sizeof(int) * c->n_scenes, cudaMemcpyHostToDevice, c->stream));
+    c->keys_valid = false;
+    c->tau_valid = false;
+    return wait_stream(c);
+}
+
+// Shared driver of mpm_backward and mpm_backward_state: stages host buffers
+// through the tape's io area (inputs are consumed by the seed kernel before
+// any output is written there).
+static int backward_common(mpm_ctx* c, const float* const* bar_in, float* const* bar_out, float* dE, float* dnu,
+                           float* dmu, float* dlam, int mem)
+{
+    if (!c || (mem != MPM_MEM_HOST && mem != MPM_MEM_DEVICE)) return MPM_ERR_INVALID_ARGUMENT;
+    if (!c->tape || !c->recording) return MPM_ERR_STATE;
+    if (any_rigid(c)) return MPM_ERR_STATE;
+    mpm_tape* t = c->tape;
+    const int N = c->total_particles;
+    const size_t cap = c->cap;
+    int st = upload_scenes(c);
+    if (st) return st;
+    SeedIn seeds{};
+    AdjOut outs{};
+    size_t off[4];
+    for (int f = 0, o = 0; f < 4; o += kComps[f], ++f) off[f] = (size_t)o * cap;  // 0, 3, 6, 15 (x cap)
+    for (int f = 0; f < 4; ++f) {
+        const float* in = bar_in ? bar_in[f] : nullptr;
+        if (in && mem == MPM_MEM_HOST) {
+            float* d = t->io + off[f];
+            MPM_CKA(cudaMemcpyAsync(d, in, sizeof(float) * kComps[f] * N, cudaMemcpyHostToDevice, c->stream));
+            in = d;
         }
-        if (N > 0) k_adj_out<<<n_blocks(N, 256), 256, 0, c->stream>>>(a, st0, adj[nxt], gmu, glam, oE, onu, ov0);
-        MPM_CKA(cudaGetLastError());
-        MPM_CKA(cudaMemcpyAsync(c->d_time, t_save.data(), sizeof(double) * c->n_scenes, cudaMemcpyHostToDevice, c->stream));
-        MPM_CKA(cudaMemcpyAsync(c->d_epoch, e_save.data(), sizeof(int) * c->n_scenes, cudaMemcpyHostToDevice, c->stream));
-        c->keys_valid = false;
-        c->tau_valid = false;
-        if ((st = wait_stream(c))) return st;
-        if (mem == MPM_MEM_HOST) {
-            if (dLdE) MPM_CKA(cudaMemcpy(dLdE, oE, sizeof(float) * N, cudaMemcpyDeviceToHost));
-            if (dLdnu) MPM_CKA(cudaMemcpy(dLdnu, onu, sizeof(float) * N, cudaMemcpyDeviceToHost));
-            if (dLdv0) MPM_CKA(cudaMemcpy(dLdv0, ov0, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost));
-        }
+        seeds.bar[f] = in;
+        float* out = bar_out ? bar_out[f] : nullptr;
+        outs.bar[f] = (out && mem == MPM_MEM_HOST) ? t->io + off[f] : out;
+    }
+    float* host_scalar[4] = {dE, dnu, dmu, dlam};
+    float** dev_scalar[4] = {&outs.dE, &outs.dnu, &outs.dmu, &outs.dlam};
+    for (int k = 0; k < 4; ++k)
+        *dev_scalar[k] = (host_scalar[k] && mem == MPM_MEM_HOST) ? t->io + (24 + k) * cap : host_scalar[k];
+    if ((st = backward_device(c, seeds, outs))) return st;
+    if (mem == MPM_MEM_HOST) {
+        for (int f = 0; f < 4; ++f)
+            if (bar_out && bar_out[f])
+                MPM_CKA(cudaMemcpy(bar_out[f], outs.bar[f], sizeof(float) * kComps[f] * N, cudaMemcpyDeviceToHost));
+        for (int k = 0; k < 4; ++k)
+            if (host_scalar[k]) MPM_CKA(cudaMemcpy(host_scalar[k], *dev_scalar[k], sizeof(float) * N, cudaMemcpyDeviceToHost));
     }
     return MPM_OK;
+}
+
+extern "C" int mpm_backward(mpm_ctx* c, const float* dLdx, const float* dLdv, float* dLdE, float* dLdnu,
+                            float* dLdv0, int mem)
+{
+    const float* in[4] = {dLdx, dLdv, nullptr, nullptr};
+    float* out[4] = {nullptr, dLdv0, nullptr, nullptr};
+    return backward_common(c, in, out, dLdE, dLdnu, nullptr, nullptr, mem);
+}
+
+extern "C" int mpm_backward_state(mpm_ctx* c, const float* const* bar_in, float* const* bar_out, float* dL_dmu,
+                                  float* dL_dlam, int mem)
+{
+    return backward_common(c, bar_in, bar_out, nullptr, nullptr, dL_dmu, dL_dlam, mem);
 }

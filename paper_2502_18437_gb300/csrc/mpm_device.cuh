@@ -59,6 +59,15 @@ struct RigidCur {
     float pts[kMaxPts * 3];
 };
 
+// Pose of a solid rigid (sphere, box) at the end of the substep, for the
+// particle push-out at the end of G2P.
+struct SolidPose {
+    int type;
+    float c[3], R[9];
+    float radius;
+    float half[3];
+};
+
 struct PState {
     float* x;
     float* v;
@@ -74,7 +83,7 @@ struct PState {
 enum {
     CTR_N_ACT = 0,     // active particle bricks
     CTR_N_NACT = 1,    // active node bricks
-    CTR_SPARE = 2,
+    CTR_DONE_G2P = 2,  // CTAs of the G2P launch that have finished (the last one advances the clocks)
     CTR_WORK_P2G = 3,  // dynamic work counters of the persistent kernels
     CTR_WORK_GRID = 4,
     CTR_WORK_G2P = 5,

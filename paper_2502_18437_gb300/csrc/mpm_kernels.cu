@@ -597,31 +597,15 @@ __device__ bool rigid_contact(const RigidCur& R, float3 x, float m, float3& v, f
 
 __device__ void stage_rigid(const RigidDev& src, double t_now, RigidCur& dst)
 {
-    const float tau = (float)(t_now - src.t_set);
     dst.type = src.type;
     dst.n_pts = src.n_pts;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        dst.c[i] = src.c0[i] + tau * src.vel[i];
         dst.vel[i] = src.vel[i];
         dst.omega[i] = src.omega[i];
         dst.half[i] = src.half[i];
     }
-    // q(tau) = exp(tau omega / 2) * q0
-    const float wx = src.omega[0], wy = src.omega[1], wz = src.omega[2];
-    const float wn = sqrtf(wx * wx + wy * wy + wz * wz);
-    float qw = src.q0[0], qx = src.q0[1], qy = src.q0[2], qz = src.q0[3];
-    if (wn > 0.f) {
-        float sh, ch;
-        sincosf(0.5f * wn * tau, &sh, &ch);
-        const float ax = wx / wn * sh, ay = wy / wn * sh, az = wz / wn * sh;
-        const float nw = ch * qw - ax * qx - ay * qy - az * qz;
-        const float nx = ch * qx + ax * qw + ay * qz - az * qy;
-        const float ny = ch * qy - ax * qz + ay * qw + az * qx;
-        const float nz = ch * qz + ax * qy - ay * qx + az * qw;
-        qw = nw; qx = nx; qy = ny; qz = nz;
-    }
-    quat_to_mat(qw, qx, qy, qz, dst.R);
+    rigid_pose_at(src, t_now, dst.c, dst.R);
     dst.mu_k = src.mu_k;
     dst.c_d = src.c_d;
     dst.margin = src.margin;
@@ -828,6 +812,8 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // sX[d * stride] and sF[q * stride] by cp.async one particle ahead; this call
 // starts the copies of particle pnext (when >= 0) as soon as its own values
 // are out of the buffers: x after the gather, F after the F update.
+// The new position is returned in o.x and stored by the caller, after the
+// particle push-out (finish_position).
 __device__ __forceinline__ unsigned g2p_particle(const StepArgs& a, const SceneDev& sc, const float4* lin, int p, int s,
                                                  int ox, int oy, int oz, G2POut& o, float* sX = nullptr,
                                                  float* sF = nullptr, int stride = 0, int pnext = -1)
@@ -896,10 +882,7 @@ __device__ __forceinline__ unsigned g2p_particle(const StepArgs& a, const SceneD
     o.x[1] = x1 + dt * v1;
     o.x[2] = x2 + dt * v2;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        a.out.x[(size_t)d * cap + s] = o.x[d];
-        a.out.v[(size_t)d * cap + s] = o.v[d];
-    }
+    for (int d = 0; d < 3; ++d) a.out.v[(size_t)d * cap + s] = o.v[d];
 #pragma unroll
     for (int i = 0; i < 9; ++i) a.out.C[(size_t)i * cap + s] = o.C[i];
     a.out.id[s] = a.in.id[p];
@@ -933,11 +916,21 @@ __device__ __forceinline__ unsigned g2p_particle(const StepArgs& a, const SceneD
     ebits |= constitutive(a.model, a.plasticity, a.yield_stress, mu, lam, Fn, o.t6);
 #pragma unroll
     for (int i = 0; i < 9; ++i) a.out.F[(size_t)i * cap + s] = Fn[i];
-    float chk = o.x[0] + o.x[1] + o.x[2] + v0 + v1 + v2;
+    float chk = x0 + x1 + x2 + v0 + v1 + v2;
 #pragma unroll
     for (int i = 0; i < 9; ++i) chk += Fn[i];
     if (!isfinite(chk)) ebits |= MPM_EBIT_NONFINITE;
     return ebits;
+}
+
+// Push-out against the scene's solid rigids at the end of the substep
+// (n_solid = 0: none), then the position store at slot s.
+__device__ __forceinline__ void finish_position(const StepArgs& a, const SolidPose* poses, int n_solid, int s,
+                                                float x[3])
+{
+    if (n_solid) push_out(poses, n_solid, x);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) a.out.x[(size_t)d * a.cap + s] = x[d];
 }
 
 // Copy the 6^3 window out of the 2x2x2 staged bricks into a linear array, so
@@ -952,8 +945,10 @@ __device__ __forceinline__ void linearize_window(const float4* vw, float4* lin)
 }
 
 // MINB = CTAs per SM the registers must allow (768/BLOCK: 80 registers;
-// 1024/BLOCK: 64 registers with a few spills, more warps in flight).
-template <int BLOCK, int MINB>
+// 1024/BLOCK: 64 registers, more warps in flight).  SOLIDS: some scene of the
+// launch has a rigid, so particles may need the push-out (a separate variant:
+// its extra live registers would make the 64-register build spill).
+template <int BLOCK, int MINB, bool SOLIDS>
 __global__ void __launch_bounds__(BLOCK, MINB) k_g2p(StepArgs a)
 {
     // x and F of each thread's next particle, copied by cp.async one particle ahead
@@ -962,18 +957,25 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_g2p(StepArgs a)
     __shared__ __align__(16) float4 lin[kWinNodes];
     __shared__ __align__(8) unsigned long long bar[2];
     __shared__ int s_item[2];
+    __shared__ SolidPose s_pose[kMaxRigids];  // the scene's rigids at the end of the substep
+    __shared__ int s_pose_scene;
     const int tid = threadIdx.x;
     const int n_act = a.sb.counters[CTR_N_ACT];
     int* work = &a.sb.counters[CTR_WORK_G2P];
+    if (tid == 0) s_pose_scene = -1;
     walker_init<BLOCK>(a, n_act, vw, bar, s_item, work);
     unsigned phase[2] = {0u, 0u};
     int buf = 0;
     for (;;) {
         const int item = s_item[buf];
         if (item >= n_act) break;
-        if (!walker_next(a, n_act, vw, bar, s_item, work, buf, phase, item)) return;
+        if (!walker_next(a, n_act, vw, bar, s_item, work, buf, phase, item)) break;
         const int start = a.sb.act_start[item], count = a.sb.act_count[item], scene = a.sb.act_scene[item];
         const SceneDev sc = a.scenes[scene];
+        // s_pose_scene changes only after the barrier below, which every thread
+        // passes after this test
+        const int n_solid = SOLIDS ? sc.n_rigid : 0;
+        if (n_solid && scene != s_pose_scene) stage_solids(a, scene, s_pose);
         const int nb = sc.nb, lb = a.sb.act_brick[item] - sc.brick_base;
         const int ox = (lb / (nb * nb)) * 4, oy = ((lb / nb) % nb) * 4, oz = (lb % nb) * 4;
         // the brick's first particle of each thread: its copies start here (the
@@ -987,6 +989,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_g2p(StepArgs a)
         }
         linearize_window<BLOCK>(vw[buf], lin);
         __syncthreads();
+        if (tid == 0 && n_solid) s_pose_scene = scene;
         unsigned ebits = 0;
         for (int k0 = 0; k0 < count; k0 += BLOCK) {
             const int k = k0 + tid;
@@ -999,6 +1002,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_g2p(StepArgs a)
                 pcur = pnext;
 #pragma unroll
                 for (int q = 0; q < 6; ++q) a.out.tau[(size_t)q * a.cap + start + k] = o.t6[q];
+                finish_position(a, SOLIDS ? s_pose : nullptr, n_solid, start + k, o.x);
                 unsigned ood = 0;
                 key = cell_key(sc, o.x[0], o.x[1], o.x[2], ood);
                 if (ood && !(ebits & MPM_EBIT_NONFINITE)) ebits |= MPM_EBIT_OUT_OF_DOMAIN;
@@ -1013,6 +1017,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_g2p(StepArgs a)
         __syncthreads();
         buf ^= 1;
     }
+    walker_exit(a);
 }
 
 // ------------------------------------------------------- fused G2P + P2G
@@ -1038,11 +1043,14 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_g2p2g(StepArgs a)
     __shared__ int cell_cnt[64], cell_off[65];
     __shared__ __align__(8) unsigned long long bar[2];
     __shared__ int s_item[2];
+    __shared__ SolidPose s_pose[kMaxRigids];  // the scene's rigids at the end of the substep
+    __shared__ int s_pose_scene;
     const int tid = threadIdx.x;
     const int cell = tid & 63, slice = tid >> 6;
     const int cx = cell >> 4, cy = (cell >> 2) & 3, cz = cell & 3;
     const int n_act = a.sb.counters[CTR_N_ACT];
     int* work = &a.sb.counters[CTR_WORK_G2P];
+    if (tid == 0) s_pose_scene = -1;
     walker_init<kFusedThreads>(a, n_act, vw, bar, s_item, work);
     unsigned phase[2] = {0u, 0u};
     int buf = 0;
@@ -1051,9 +1059,11 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_g2p2g(StepArgs a)
         if (item >= n_act) break;
         for (int t = tid; t < 4 * kW8Nodes; t += kFusedThreads) (&win[0][0])[t] = 0.0f;
         if (tid < 64) cell_cnt[tid] = 0;
-        if (!walker_next(a, n_act, vw, bar, s_item, work, buf, phase, item)) return;
+        if (!walker_next(a, n_act, vw, bar, s_item, work, buf, phase, item)) break;
         const int start = a.sb.act_start[item], count = a.sb.act_count[item], scene = a.sb.act_scene[item];
         const SceneDev sc = a.scenes[scene];
+        const int n_solid = a.any_rigid ? sc.n_rigid : 0;
+        if (n_solid && scene != s_pose_scene) stage_solids(a, scene, s_pose);
         const int n = sc.n, nb = sc.nb, lb = a.sb.act_brick[item] - sc.brick_base;
         const int ox = (lb / (nb * nb)) * 4, oy = ((lb / nb) % nb) * 4, oz = (lb % nb) * 4;
         const float fn = (float)n, dxs = 1.0f / fn;
@@ -1061,6 +1071,7 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_g2p2g(StepArgs a)
         const float kA = a.dt * sc.V0 * 4.0f * fn * fn;
         linearize_window<kFusedThreads>(vw[buf], lin);
         __syncthreads();
+        if (tid == 0 && n_solid) s_pose_scene = scene;
         unsigned ebits = 0;
         for (int k0 = 0; k0 < count; k0 += kFusedThreads) {
             const int k = k0 + tid;
@@ -1069,6 +1080,7 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_g2p2g(StepArgs a)
             if (valid) {
                 G2POut o;
                 ebits |= g2p_particle(a, sc, lin, a.sb.perm[start + k], start + k, ox, oy, oz, o);
+                finish_position(a, s_pose, n_solid, start + k, o.x);
                 // P2G of the next substep at the new position
                 int bc[3];
                 float f[3], w[9];
@@ -1154,6 +1166,7 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_g2p2g(StepArgs a)
         __syncthreads();
         buf ^= 1;
     }
+    walker_exit(a);
 }
 
 // ------------------------------------------------------- state I/O kernels
@@ -1270,22 +1283,29 @@ cudaError_t launch_grid(const StepArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_g2p(const StepArgs& a, cudaStream_t s)
+template <bool SOLIDS>
+static void launch_g2p_variant(const StepArgs& a, cudaStream_t s)
 {
     const int c = a.persistent_ctas;
     if (a.g2p_regs64) {
         switch (a.g2p_threads) {
-        case 128: k_g2p<128, 8><<<c, 128, 0, s>>>(a); break;
-        case 512: k_g2p<512, 2><<<c, 512, 0, s>>>(a); break;
-        default: k_g2p<256, 4><<<c, 256, 0, s>>>(a); break;
+        case 128: k_g2p<128, 8, SOLIDS><<<c, 128, 0, s>>>(a); break;
+        case 512: k_g2p<512, 2, SOLIDS><<<c, 512, 0, s>>>(a); break;
+        default: k_g2p<256, 4, SOLIDS><<<c, 256, 0, s>>>(a); break;
         }
     } else {
         switch (a.g2p_threads) {
-        case 128: k_g2p<128, 6><<<c, 128, 0, s>>>(a); break;
-        case 512: k_g2p<512, 1><<<c, 512, 0, s>>>(a); break;
-        default: k_g2p<256, 3><<<c, 256, 0, s>>>(a); break;
+        case 128: k_g2p<128, 6, SOLIDS><<<c, 128, 0, s>>>(a); break;
+        case 512: k_g2p<512, 1, SOLIDS><<<c, 512, 0, s>>>(a); break;
+        default: k_g2p<256, 3, SOLIDS><<<c, 256, 0, s>>>(a); break;
         }
     }
+}
+
+cudaError_t launch_g2p(const StepArgs& a, cudaStream_t s)
+{
+    if (a.any_rigid) launch_g2p_variant<true>(a, s);
+    else launch_g2p_variant<false>(a, s);
     return cudaGetLastError();
 }
 
@@ -1353,15 +1373,17 @@ int occupancy_p2g(int chunk)
 
 int occupancy_g2p(int threads, int regs64)
 {
+    // the variant with the push-out uses the same registers and a little more
+    // shared memory; its occupancy bounds both
     int b = 0;
     if (regs64) {
-        if (threads == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<128, 8>, 128, 0);
-        else if (threads == 512) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<512, 2>, 512, 0);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<256, 4>, 256, 0);
+        if (threads == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<128, 8, true>, 128, 0);
+        else if (threads == 512) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<512, 2, true>, 512, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<256, 4, true>, 256, 0);
     } else {
-        if (threads == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<128, 6>, 128, 0);
-        else if (threads == 512) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<512, 1>, 512, 0);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<256, 3>, 256, 0);
+        if (threads == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<128, 6, true>, 128, 0);
+        else if (threads == 512) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<512, 1, true>, 512, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<256, 3, true>, 256, 0);
     }
     return b;
 }

@@ -12,7 +12,8 @@
 // every call on that device and kept until the process exits.  Host code
 // only sees a stand-in for its name, so the device address is obtained with
 // cudaGetSymbolAddress once per device, on the first call made with that
-// device current.  Calls that overlap on the GPU (different streams or host
+// device current (and again if that device's context was reset and
+// recreated, which the context id tells).  Calls that overlap on the GPU (different streams or host
 // threads) use the same scratch and race: serialise them.
 #include <mutex>
 
@@ -122,6 +123,8 @@ __global__ void __launch_bounds__(kNaScanThreads) k_na_scan(NaScratch s, int nbr
     }
 }
 
+// Every slot is written exactly once: the ranks and the brick counts come from
+// the same atomics, so offsets[key] + rank covers [0, N) without gaps.
 __global__ void k_na_scatter(int N, NaScratch s, int* perm)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -130,10 +133,49 @@ __global__ void k_na_scatter(int N, NaScratch s, int* perm)
     if (dst >= 0 && dst < N) perm[dst] = i;
 }
 
-std::mutex g_mu;
-int* g_addr[64] = {};
+// Driver calls reached through the runtime (no link against libcuda): the
+// current context and its unique id, so that a cached address is never used
+// in a context other than the one it was looked up in (a cudaDeviceReset
+// destroys the primary context; the next one gets a new id).
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
 
-// Device address of the scratch array on the current device (set up once).
+struct ScratchSlot {
+    unsigned long long ctx_id = 0;
+    int* addr = nullptr;
+};
+
+std::mutex g_mu;
+ScratchSlot g_slot[64];
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+bool g_driver_looked_up = false;
+
+// Id of the current context, 0 when the driver entry points are unavailable.
+unsigned long long current_context_id()
+{
+    if (!g_driver_looked_up) {
+        g_driver_looked_up = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_id = reinterpret_cast<CtxGetIdFn>(f);
+        cudaGetLastError();
+    }
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_current && g_ctx_id && g_ctx_current(&ctx) == 0 && ctx && g_ctx_id(ctx, &id) == 0) return id;
+    return 0;
+}
+
+// Device address of the scratch array in the current device's context: looked
+// up with cudaGetSymbolAddress on the first call with that device (and
+// context) current, then reused.
 cudaError_t scratch_address(int** out)
 {
     int dev = 0;
@@ -141,13 +183,24 @@ cudaError_t scratch_address(int** out)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
+    // make sure the device's context exists before asking for its id
+    if (!g_slot[dev].addr) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess) return e;
-        g_addr[dev] = static_cast<int*>(p);
+        g_slot[dev].addr = static_cast<int*>(p);
+        g_slot[dev].ctx_id = current_context_id();
+    } else {
+        const unsigned long long id = current_context_id();
+        if (id != g_slot[dev].ctx_id) {  // the context was reset and recreated
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_scratch);
+            if (e != cudaSuccess) return e;
+            g_slot[dev].addr = static_cast<int*>(p);
+            g_slot[dev].ctx_id = id;
+        }
     }
-    *out = g_addr[dev];
+    *out = g_slot[dev].addr;
     return cudaSuccess;
 }
 

@@ -419,10 +419,10 @@ __device__ __forceinline__ void issue_halo(const StepArgs& a, int item, float4* 
     }
 }
 
-// Shared prologue of the brick-walking kernels: mbarriers, first halo, clocks.
+// Shared prologue of the brick-walking kernels: mbarriers, first halo.
 template <int BLOCK>
 __device__ __forceinline__ void walker_init(const StepArgs& a, int n_act, float4 (*vw)[8 * 64], unsigned long long* bar,
-                                            int* s_item, int* work, bool advance_clocks = true)
+                                            int* s_item, int* work)
 {
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -433,14 +433,109 @@ __device__ __forceinline__ void walker_init(const StepArgs& a, int n_act, float4
         s_item[0] = first;
         if (first < n_act) issue_halo(a, first, vw[0], &bar[0]);
     }
-    if (advance_clocks && blockIdx.x == 0) {
-        // scene clocks advance once per substep (read by the next grid update)
-        for (int s = a.r.s0 + tid; s < a.r.s1; s += BLOCK) {
-            a.t_scene[s] += (double)a.dt;
-            a.epoch[s] += 1;
+    __syncthreads();
+}
+
+// Epilogue of the forward G2P launches, run by every CTA on its way out: the
+// last CTA to finish advances the scene clocks and substep counters (read by
+// the next grid update and the state readback).  No CTA of the launch reads a
+// clock after it has counted itself out, so the clocks stay constant while
+// G2P evaluates rigid poses at the end of the substep.
+__device__ __forceinline__ void walker_exit(const StepArgs& a)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int done = atomicAdd(&a.sb.counters[CTR_DONE_G2P], 1);
+        if (done == (int)gridDim.x - 1) {
+            __threadfence();
+            for (int s = a.r.s0; s < a.r.s1; ++s) {
+                a.t_scene[s] += (double)a.dt;
+                a.epoch[s] += 1;
+            }
+            a.sb.counters[CTR_DONE_G2P] = 0;
         }
     }
-    __syncthreads();
+}
+
+// Poses at the end of the substep (clock + dt) of the solid rigids of a scene,
+// staged in shared memory by the threads tid < kMaxRigids; returns the rigid
+// slots in use (shapes other than sphere and box are staged with type -1).
+__device__ __forceinline__ void rigid_pose_at(const RigidDev& src, double t_now, float c[3], float R[9])
+{
+    const float tau = (float)(t_now - src.t_set);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) c[i] = src.c0[i] + tau * src.vel[i];
+    // q(tau) = exp(tau omega / 2) * q0
+    const float wx = src.omega[0], wy = src.omega[1], wz = src.omega[2];
+    const float wn = sqrtf(wx * wx + wy * wy + wz * wz);
+    float qw = src.q0[0], qx = src.q0[1], qy = src.q0[2], qz = src.q0[3];
+    if (wn > 0.f) {
+        float sh, ch;
+        sincosf(0.5f * wn * tau, &sh, &ch);
+        const float ax = wx / wn * sh, ay = wy / wn * sh, az = wz / wn * sh;
+        const float nw = ch * qw - ax * qx - ay * qy - az * qz;
+        const float nx = ch * qx + ax * qw + ay * qz - az * qy;
+        const float ny = ch * qy - ax * qz + ay * qw + az * qx;
+        const float nz = ch * qz + ax * qy - ay * qx + az * qw;
+        qw = nw; qx = nx; qy = ny; qz = nz;
+    }
+    quat_to_mat(qw, qx, qy, qz, R);
+}
+
+__device__ __forceinline__ void stage_solids(const StepArgs& a, int scene, SolidPose* poses)
+{
+    const int tid = threadIdx.x;
+    const int nr = a.scenes[scene].n_rigid;
+    if (tid < nr) {
+        const RigidDev& src = a.rigids[scene * kMaxRigids + tid];
+        SolidPose& P = poses[tid];
+        P.type = (src.type == MPM_SPHERE || src.type == MPM_BOX) ? src.type : -1;
+        rigid_pose_at(src, a.t_scene[scene] + (double)a.dt, P.c, P.R);
+        P.radius = src.radius;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) P.half[i] = src.half[i];
+    }
+}
+
+// Particle push-out (Sec. IV-A): a particle that ends the substep inside a
+// solid rigid (sdf < 0 at the rigid's pose at the end of the substep) moves
+// to the nearest surface point, x - sdf(x) n(x); rigids in id order.  Blades
+// and line segments push nothing out (the tissue closes around them).
+__device__ __forceinline__ void push_out(const SolidPose* poses, int nr, float x[3])
+{
+    for (int r = 0; r < nr; ++r) {
+        const SolidPose& P = poses[r];
+        if (P.type == MPM_SPHERE) {
+            const float d0 = x[0] - P.c[0], d1 = x[1] - P.c[1], d2 = x[2] - P.c[2];
+            const float l = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+            if (l < P.radius) {
+                if (l > 0.f) {
+                    const float k = P.radius / l;
+                    x[0] = P.c[0] + k * d0;
+                    x[1] = P.c[1] + k * d1;
+                    x[2] = P.c[2] + k * d2;
+                } else {  // at the centre: along the body y axis
+                    x[0] = P.c[0] + P.radius * P.R[1];
+                    x[1] = P.c[1] + P.radius * P.R[4];
+                    x[2] = P.c[2] + P.radius * P.R[7];
+                }
+            }
+        } else if (P.type == MPM_BOX) {
+            const float d0 = x[0] - P.c[0], d1 = x[1] - P.c[1], d2 = x[2] - P.c[2];
+            float p[3] = {P.R[0] * d0 + P.R[3] * d1 + P.R[6] * d2, P.R[1] * d0 + P.R[4] * d1 + P.R[7] * d2,
+                          P.R[2] * d0 + P.R[5] * d1 + P.R[8] * d2};
+            const float q0 = fabsf(p[0]) - P.half[0], q1 = fabsf(p[1]) - P.half[1], q2 = fabsf(p[2]) - P.half[2];
+            if (q0 < 0.f && q1 < 0.f && q2 < 0.f) {
+                // nearest face: the axis of the largest q (ties to the lower axis)
+                const int ax = (q0 >= q1 && q0 >= q2) ? 0 : (q1 >= q2 ? 1 : 2);
+                p[ax] = p[ax] >= 0.f ? P.half[ax] : -P.half[ax];
+                x[0] = P.c[0] + P.R[0] * p[0] + P.R[1] * p[1] + P.R[2] * p[2];
+                x[1] = P.c[1] + P.R[3] * p[0] + P.R[4] * p[1] + P.R[5] * p[2];
+                x[2] = P.c[2] + P.R[6] * p[0] + P.R[7] * p[1] + P.R[8] * p[2];
+            }
+        }
+    }
 }
 
 // Prefetch the next brick's halo and wait for this one; false on timeout (the

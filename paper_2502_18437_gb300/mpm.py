@@ -79,6 +79,7 @@ _SIGS = {
     "mpm_scene_count": (ct.c_int, [_P, ct.c_int, ct.POINTER(ct.c_int64)]),
     "mpm_tape_begin": (ct.c_int, [_P]),
     "mpm_backward": (ct.c_int, [_P, _P, _P, _P, _P, _P, ct.c_int]),
+    "mpm_backward_state": (ct.c_int, [_P, ct.POINTER(_P), ct.POINTER(_P), _P, _P, ct.c_int]),
     "mpm_autotune": (ct.c_int, [_P, ct.c_float, ct.c_int, ct.POINTER(ct.c_float)]),
     "mpm_phase_stats": (ct.c_int, [_P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64), ct.POINTER(ct.c_int64),
                                    ct.c_int]),
@@ -181,6 +182,12 @@ def mpm_tape_begin(h):
 
 def mpm_backward(h, dx, dv, dE, dnu, dv0, mem):
     return _check(lib().mpm_backward(h, dx, dv, dE, dnu, dv0, mem), "mpm_backward")
+
+
+def mpm_backward_state(h, bar_in, bar_out, dmu, dlam, mem):
+    ins = (_P * 4)(*[p or None for p in bar_in]) if bar_in is not None else None
+    outs = (_P * 4)(*[p or None for p in bar_out]) if bar_out is not None else None
+    return _check(lib().mpm_backward_state(h, ins, outs, dmu, dlam, mem), "mpm_backward_state")
 
 
 def mpm_autotune(h, dt, trial_substeps):
@@ -423,6 +430,27 @@ class Simulation:
             ins.append((p, k))
         mpm_backward(self.h, ins[0][0], ins[1][0], ptr(outs[0]), ptr(outs[1]), ptr(outs[2]), mem)
         return outs
+
+    def backward_state(self, bar=None, *, want=("x", "v", "C", "F")):
+        """Adjoint of the state at tape_begin from the adjoint of the final state.
+        ``bar``: dict field -> (N,3) / (N,3,3) float32 numpy array (missing = 0).
+        Returns a dict with the wanted fields' adjoints and "mu", "lam"."""
+        n = sum(self.count(s) for s in range(self.n_scenes))
+        bar = bar or {}
+        shapes = {"x": (n, 3), "v": (n, 3), "C": (n, 3, 3), "F": (n, 3, 3)}
+        keep, ins = [], []
+        for f in ("x", "v", "C", "F"):
+            if f in bar:
+                a = np.ascontiguousarray(np.asarray(bar[f], dtype=np.float32).reshape(shapes[f]))
+                keep.append(a)
+                ins.append(a.ctypes.data)
+            else:
+                ins.append(None)
+        out = {f: np.zeros(shapes[f], np.float32) for f in want}
+        outs = [out[f].ctypes.data if f in out else None for f in ("x", "v", "C", "F")]
+        out["mu"], out["lam"] = np.zeros(n, np.float32), np.zeros(n, np.float32)
+        mpm_backward_state(self.h, ins, outs, out["mu"].ctypes.data, out["lam"].ctypes.data, MEM_HOST)
+        return out
 
     def autotune(self, dt, trial_substeps=5):
         return mpm_autotune(self.h, dt, trial_substeps)

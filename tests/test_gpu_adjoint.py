@@ -110,3 +110,105 @@ def test_adjoint_refuses_what_it_does_not_differentiate():
         sim.substep(sc["dt"], 2)
         with pytest.raises(mpm.MPMError):
             sim.backward(np.zeros((len(sc["x"]), 3), np.float32))
+
+
+def test_adjoint_full_size_single_coordinates():
+    # The differentiable workload at full size (32,768 particles, 64^3, 200
+    # substeps, a checkpoint every 20): single coordinates of E (relative step),
+    # nu and the three components of v0 on a seeded sample of particles plus the
+    # particle of largest |E dL/dE|, each against its own FP64 central
+    # difference (the oracle runs in spawned worker processes).
+    from tests.oracle_pool import diff_cube_loss, map_tasks
+
+    sc = W.diff_cube()
+    steps = sc["substeps"]
+    L, gE, gnu, gv0 = gpu_grads(sc, steps, 20)
+    N = len(sc["x"])
+    g = np.random.default_rng(11)
+    idx = [int(i) for i in g.choice(N, 3, replace=False)] + [int(np.argmax(np.abs(gE * sc["E"])))]
+    coords = [("E", 0), ("nu", 0), ("v0", 0), ("v0", 1), ("v0", 2)]
+    tasks = [({}, steps, [(k, i, d, s * H)]) for i in idx for k, d in coords for s in (1, -1)]
+    losses = np.array(map_tasks(diff_cube_loss, tasks)).reshape(len(idx), len(coords), 2)
+    scale = {"E": np.abs(gE * sc["E"]).max(), "nu": np.abs(gnu).max(), "v0": np.abs(gv0).max()}
+    for a, i in enumerate(idx):
+        for b, (k, d) in enumerate(coords):
+            fd = (losses[a, b, 0] - losses[a, b, 1]) / (2 * H)
+            got = {"E": gE[i] * sc["E"][i], "nu": gnu[i], "v0": gv0[i, d]}[k]
+            print(f"particle {i} {k}[{d}]: adjoint {got:.6e} fd {fd:.6e}")
+            assert abs(got - fd) <= TOL * abs(fd) + 1e-6 * scale[k], (i, k, d, got, fd)
+
+
+# ---------------------------------------------- dot-product tests per block
+#
+# For the substep map s_0 -> s_T (s = x, v, C, F per particle; mu, lambda as
+# parameters) the adjoint must satisfy <J u, w> = <u, J^T w> for every input
+# direction u and output weight w.  J u comes from FP64 central differences of
+# the oracle, J^T w from the hand-written adjoint kernels (mpm_backward_state).
+# Taking u and w inside one block each checks one path through the reverse
+# kernels, e.g. (F -> v): the stress VJP of P2G^-1 (polar derivative for
+# fixed-corotated), the grid^-1 normalisation and G2P^-1's gather; (C -> C):
+# P2G^-1's affine term and G2P^-1's B-matrix; (x -> x): the weight-gradient
+# terms of both transfers; (mu, lambda -> *): the material VJP.
+
+IN_BLOCKS = ("x", "v", "C", "F", "mu", "lam")
+OUT_BLOCKS = ("x", "v", "C", "F")
+
+
+def _perturbed_state(sc, seed):
+    g = np.random.default_rng(seed)
+    N = len(sc["x"])
+    v = (sc["v"] + 0.05 * g.normal(size=(N, 3))).astype(np.float32)
+    C = (0.5 * g.normal(size=(N, 3, 3))).astype(np.float32)
+    F = (np.eye(3) + 0.02 * g.normal(size=(N, 3, 3))).astype(np.float32)
+    return v, C, F
+
+
+def _oracle_out(sc, x, v, C, F, mu, lam, steps):
+    st = oracle.State(x, v, C, F, mu=mu, lam=lam)
+    assert oracle.run(oracle.config_from_workload(sc), st, sc["dt"], steps) == 0
+    return {"x": st.x, "v": st.v, "C": st.C, "F": st.F}
+
+
+@pytest.mark.parametrize("model,steps", [("fixed_corotated", 1), ("neo_hookean", 1), ("fixed_corotated", 6)])
+def test_adjoint_dot_product_per_block(model, steps):
+    sc = W.diff_cube(n=32, n_side=10, substeps=steps, model=model)
+    N = len(sc["x"])
+    v, C, F = _perturbed_state(sc, 5)
+    x = sc["x"]
+    mu, lam = oracle.lame_arrays(sc["E"], sc["nu"])
+    g = np.random.default_rng(6)
+    base = {"x": x.astype(np.float64), "v": v.astype(np.float64), "C": C.astype(np.float64),
+            "F": F.astype(np.float64), "mu": mu, "lam": lam}
+    # GPU: J^T w for one weight per output block
+    with mpm.Simulation(32, N, model=model, tape_checkpoint_every=max(1, steps // 2),
+                        tape_max_substeps=steps) as sim:
+        sim.add_particles(0, x, sc["v"], sc["E"], sc["nu"], rho=sc["rho"], V0=sc["V0"])
+        sim.write_state(0, v=v, C=C, F=F)
+        sim.tape_begin()
+        sim.substep(sc["dt"], steps)
+        ws = {b: g.normal(size=base[b].shape) for b in OUT_BLOCKS}
+        jt = {b: sim.backward_state({b: ws[b]}) for b in OUT_BLOCKS}
+    # oracle: J u by central differences, one direction per input block
+    steps_h = {"x": 1e-6, "v": 1e-6, "C": 1e-5, "F": 1e-6}
+    worst = 0.0
+    for a in IN_BLOCKS:
+        u = g.normal(size=base[a].shape)
+        h = steps_h.get(a, 1e-6)
+        args_p, args_m = dict(base), dict(base)
+        if a in ("mu", "lam"):
+            args_p[a], args_m[a] = base[a] * (1 + h * u), base[a] * (1 - h * u)
+            u = u * base[a]  # the direction in mu / lambda itself
+        else:
+            args_p[a], args_m[a] = base[a] + h * u, base[a] - h * u
+        op = _oracle_out(sc, args_p["x"], args_p["v"], args_p["C"], args_p["F"], args_p["mu"], args_p["lam"], steps)
+        om = _oracle_out(sc, args_m["x"], args_m["v"], args_m["C"], args_m["F"], args_m["mu"], args_m["lam"], steps)
+        ju = {b: (op[b] - om[b]) / (2 * h) for b in OUT_BLOCKS}
+        for b in OUT_BLOCKS:
+            fd = float(np.sum(ju[b] * ws[b]))
+            got = float(np.sum(u * jt[b][a].astype(np.float64)))
+            # the floor: FP32 rounding of the adjoint relative to the block's size
+            floor = 1e-5 * float(np.linalg.norm(ju[b]) * np.linalg.norm(ws[b]))
+            print(f"{model} T={steps} {a}->{b}: adjoint {got:.6e} fd {fd:.6e}")
+            assert abs(got - fd) <= TOL * abs(fd) + floor, (a, b, got, fd)
+            worst = max(worst, abs(got - fd) / max(abs(fd), 1e-300))
+    print(f"worst relative difference {worst:.2e}")

@@ -242,3 +242,35 @@ def test_box_contact_matches_oracle(steps_before):
     check_grid(sc, out, gm, gv, Scales(sc, F))
     assert np.abs(imp[0, :3]).max() > 0  # in contact
     assert_close("box impulse", out["impulse"][0], imp[0], rtol=1e-4, rel_scale=1e-4)
+
+
+@pytest.mark.parametrize("shape", ["sphere", "box"])
+@pytest.mark.parametrize("steps_before", [0, 8])
+def test_push_out_matches_oracle(shape, steps_before):
+    # A solid rigid sweeping through a block of particles, many of which start
+    # inside it: after each substep the particles left inside are pushed to its
+    # surface at its pose at the end of the substep (Sec. IV-A particle
+    # correction).  One substep from the same state at two points of the run.
+    sc = W.elastic_cube(n=32, n_side=14, corner=(0.32, 0.3, 0.33), substeps=20)
+    if shape == "sphere":
+        rig = W.sphere((0.43 + 0.17 / 32, 0.42 - 0.23 / 32, 0.44 + 0.11 / 32), 0.07, vel=(0.3, -0.4, 0.1),
+                       mu_k=0.2, margin=0.25 / 32)
+    else:
+        q = np.array([0.93, -0.2, 0.25, 0.18])
+        rig = W.box((0.43 + 0.17 / 32, 0.42 - 0.23 / 32, 0.44 + 0.11 / 32), (0.06, 0.04, 0.07),
+                    quat=tuple(q / np.linalg.norm(q)), vel=(-0.2, -0.3, 0.2), omega=(1.0, -2.0, 0.5), mu_k=0.2,
+                    margin=0.25 / 32)
+    sc["rigids"] = [rig]
+    v, C, F = perturbed(sc, seed=41, f_amp=0.01, c_amp=1.0)
+    x, v, C, F, out = gpu_one_step(sc, v, C, F, steps_before=steps_before)
+    st, gm, gv, err, imp = oracle_one_step(sc, x, v, C, F, steps_before)
+    assert err == 0
+    check_fields(sc, out, st, Scales(sc, F))
+    check_grid(sc, out, gm, gv, Scales(sc, F))
+    # nobody is left inside the rigid at its new pose
+    r = oracle.make_rigid(rig)
+    for _ in range(steps_before + 1):
+        oracle.rigid_advance(r, sc["dt"])
+    inside = [oracle.geometry(r, p)[3] for p in out["x"].astype(np.float64)]
+    assert min(inside) > -1e-6
+    assert np.sum(np.abs(inside) < 1e-6) > 20  # the pushed particles sit on the surface

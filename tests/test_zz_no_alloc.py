@@ -60,3 +60,27 @@ def test_noalloc_sort_rejects_sizes_beyond_its_scratch():
     assert mpm.mpm_sort_bricks_noalloc(512, 4, x.data_ptr(), p.data_ptr()) == -7
     assert mpm.mpm_sort_bricks_noalloc(64, (1 << 20) + 1, x.data_ptr(), p.data_ptr()) == -7
     assert mpm.mpm_sort_bricks_noalloc(30, 4, x.data_ptr(), p.data_ptr()) == -1
+
+
+def test_noalloc_sort_at_its_limits_and_degenerate_calls():
+    # The sizes the static scratch is built for (N = MPM_NOALLOC_MAX_PARTICLES on
+    # a 256^3 grid: 262,144 bricks + the end offset), without brick_start, and
+    # an empty input (every brick starts at 0).
+    sc = W.tissue_block(N=1 << 20, n=256)
+    n, N = sc["n"], len(sc["x"])
+    keys = brick_keys(sc["x"], n)
+    perm, start = noalloc_sort(sc["x"], n)
+    assert np.array_equal(np.sort(perm), np.arange(N))
+    assert np.all(np.diff(keys[perm]) >= 0)
+    assert np.array_equal(start, np.concatenate([[0], np.cumsum(np.bincount(keys, minlength=(n // 4) ** 3))]))
+    xd = torch.tensor(sc["x"], device="cuda")
+    p2 = torch.full((N,), -1, dtype=torch.int32, device="cuda")
+    assert mpm.mpm_sort_bricks_noalloc(n, N, xd.data_ptr(), p2.data_ptr(), None,
+                                       torch.cuda.current_stream().cuda_stream) == 0
+    torch.cuda.synchronize()
+    assert np.array_equal(keys[p2.cpu().numpy()], keys[perm])
+    start0 = torch.full(((64 // 4) ** 3 + 1,), -1, dtype=torch.int32, device="cuda")
+    assert mpm.mpm_sort_bricks_noalloc(64, 0, None, None, start0.data_ptr(),
+                                       torch.cuda.current_stream().cuda_stream) == 0
+    torch.cuda.synchronize()
+    assert not start0.cpu().numpy().any()
