@@ -92,6 +92,20 @@ def lib():
         L.orc_run.restype = ct.c_int
         L.orc_run.argtypes = [ct.POINTER(Config), ct.c_int, D, D, D, D, D, D, ct.c_int,
                               ct.POINTER(Rigid), ct.c_double, ct.c_int]
+        L.orc_bspline_dN.restype = ct.c_double
+        L.orc_bspline_dN.argtypes = [ct.c_double]
+        L.orc_p2g_standard.restype = ct.c_int
+        L.orc_p2g_standard.argtypes = [ct.POINTER(Config), ct.c_int, D, D, D, D, D, ct.c_double, D, D]
+        L.orc_g2p_standard.restype = ct.c_int
+        L.orc_g2p_standard.argtypes = [ct.POINTER(Config), ct.c_int, D, D, D, D, D, ct.c_double, D]
+        L.orc_pb_constraint.argtypes = [D, D, ct.c_double, ct.c_double, D]
+        L.orc_p2g_apic.restype = ct.c_int
+        L.orc_p2g_apic.argtypes = [ct.POINTER(Config), ct.c_int, D, D, D, D, D]
+        L.orc_g2p_vc.restype = ct.c_int
+        L.orc_g2p_vc.argtypes = [ct.POINTER(Config), ct.c_int, D, D, D, D]
+        L.orc_run_solver.restype = ct.c_int
+        L.orc_run_solver.argtypes = [ct.POINTER(Config), ct.c_int, ct.c_int, D, D, D, D, D, D, ct.c_int,
+                                     ct.POINTER(Rigid), ct.c_double, ct.c_int, ct.c_int, ct.c_double]
         L.orc_sort_by_brick.argtypes = [ct.c_int, ct.c_int, F32, I, I, I]
         L.orc_loss.restype = ct.c_double
         L.orc_loss.argtypes = [ct.c_int, D, D, D]
@@ -315,6 +329,43 @@ def run(cfg, st, dt, n_steps, rigids=None, n_rigid=0):
     x, v, C, F, mu, lam = st.ptrs()
     return lib().orc_run(ct.byref(cfg), st.N, x, v, C, F, mu, lam, int(n_rigid), rigids,
                          float(dt), int(n_steps))
+
+
+SOLVERS = {"mls": 0, "standard": 1, "pb": 2}
+
+
+def bspline_dN(r):
+    return lib().orc_bspline_dN(float(r))
+
+
+def p2g_standard(cfg, st, dt):
+    nn = cfg.n ** 3
+    gm, gmv = np.zeros(nn), np.zeros((nn, 3))
+    x, v, C, F, mu, lam = st.ptrs()
+    err = lib().orc_p2g_standard(ct.byref(cfg), st.N, x, v, F, mu, lam, float(dt), _dp(gm), _dp(gmv))
+    return gm, gmv, err
+
+
+def g2p_standard(cfg, st, gv, dt):
+    gv = _arr(gv)
+    x, v, C, F, mu, lam = st.ptrs()
+    return lib().orc_g2p_standard(ct.byref(cfg), st.N, x, v, C, F, mu, float(dt), _dp(gv))
+
+
+def pb_constraint(C, F, dt, beta):
+    C, F = _arr(C, (3, 3)), _arr(F, (3, 3))
+    out = np.zeros((3, 3))
+    lib().orc_pb_constraint(_dp(C), _dp(F), float(dt), float(beta), _dp(out))
+    return out
+
+
+def run_solver(cfg, st, dt, n_steps, solver="mls", rigids=None, n_rigid=0, iters=1, beta=1.0):
+    """n_steps steps of a solver ("mls", "standard", "pb") in place; returns the error bits."""
+    if rigids is None:
+        rigids, n_rigid = (Rigid * 1)(), 0
+    x, v, C, F, mu, lam = st.ptrs()
+    return lib().orc_run_solver(ct.byref(cfg), SOLVERS[solver], st.N, x, v, C, F, mu, lam, int(n_rigid), rigids,
+                                float(dt), int(n_steps), int(iters), float(beta))
 
 
 def sort_by_brick(n, x32):

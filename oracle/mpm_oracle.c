@@ -662,6 +662,273 @@ int orc_run(const orc_config* cfg, int N, double* x, double* v, double* C, doubl
     return err;
 }
 
+/* ------------------------------------------------------- standard MPM */
+
+/* Derivative dN/dr of the quadratic B-spline basis (textbook piecewise). */
+double orc_bspline_dN(double r)
+{
+    double a = fabs(r);
+    if (a < 0.5) return -2.0 * r;
+    if (a < 1.5) return (r > 0 ? -1.0 : 1.0) * (1.5 - a);
+    return 0.0;
+}
+
+/* Weights and their derivatives (w.r.t. the particle coordinate in cell
+ * units) of the 3 nodes base, base+1, base+2. */
+static void bspline_w_dw(double f, double w[3], double dw[3])
+{
+    for (int i = 0; i < 3; ++i) {
+        w[i] = orc_bspline_N(f - (double)i);
+        dw[i] = orc_bspline_dN(f - (double)i);
+    }
+}
+
+/* P2G of the standard MPM (Sec. III-A), PIC-style: m_I += phi m (Eq. 1),
+ * (m v)_I += phi m v (Eq. 1) plus the internal-force impulse dt f_I^int with
+ * f_I^int = -sum V sigma grad phi (Eq. 2), V sigma = V0 tau (V = J V0), so the
+ * momentum entering Eq. 3 is (m v)_I - dt V0 tau grad phi_I(x_p).  grad phi is
+ * the spatial gradient, (1/dx) times the derivative in cell units.  External
+ * force: gravity, added in the grid update as v_I += dt g (Eq. 3 with
+ * f_ext = m_I g).  gm, gmv accumulated into (caller zeroes). */
+int orc_p2g_standard(const orc_config* cfg, int N, const double* x, const double* v, const double* F,
+                     const double* mu, const double* lam, double dt, double* gm, double* gmv)
+{
+    int err = 0, n = cfg->n;
+    for (int p = 0; p < N; ++p) {
+        int b[3];
+        double f[3], w[3][3], dw[3][3];
+        int e = base_and_frac(cfg, x + 3 * p, b, f);
+        if (e) { err |= e; continue; }
+        for (int d = 0; d < 3; ++d) bspline_w_dw(f[d], w[d], dw[d]);
+        double tau[9];
+        err |= orc_kirchhoff(cfg->model, F + 9 * p, mu[p], lam[p], tau);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                for (int k = 0; k < 3; ++k) {
+                    double W = w[0][i] * w[1][j] * w[2][k];
+                    double gW[3] = {n * dw[0][i] * w[1][j] * w[2][k], n * w[0][i] * dw[1][j] * w[2][k],
+                                    n * w[0][i] * w[1][j] * dw[2][k]};
+                    int64_t I = ((int64_t)(b[0] + i) * n + (b[1] + j)) * n + (b[2] + k);
+                    gm[I] += W * cfg->m_p;
+                    for (int r = 0; r < 3; ++r)
+                        gmv[3 * I + r] += W * cfg->m_p * v[3 * p + r] -
+                                          dt * cfg->V0 * (tau[3 * r] * gW[0] + tau[3 * r + 1] * gW[1] + tau[3 * r + 2] * gW[2]);
+                }
+    }
+    return err;
+}
+
+/* G2P of the standard MPM (Sec. III-A): v_p = sum phi v_I and x += dt v_p
+ * (Eq. 4), L = sum v_I grad phi^T and F = (I + dt L) F (Eq. 5), then the
+ * plastic projection when enabled.  L is stored in C (the velocity gradient
+ * the F update used; the standard P2G does not read it). */
+int orc_g2p_standard(const orc_config* cfg, int N, double* x, double* v, double* C, double* F,
+                     const double* mu, double dt, const double* gv)
+{
+    int err = 0, n = cfg->n;
+    for (int p = 0; p < N; ++p) {
+        int b[3];
+        double f[3], w[3][3], dw[3][3];
+        int e = base_and_frac(cfg, x + 3 * p, b, f);
+        if (e) { err |= e; continue; }
+        for (int d = 0; d < 3; ++d) bspline_w_dw(f[d], w[d], dw[d]);
+        double vp[3] = {0, 0, 0}, L[9] = {0};
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                for (int k = 0; k < 3; ++k) {
+                    double W = w[0][i] * w[1][j] * w[2][k];
+                    double gW[3] = {n * dw[0][i] * w[1][j] * w[2][k], n * w[0][i] * dw[1][j] * w[2][k],
+                                    n * w[0][i] * w[1][j] * dw[2][k]};
+                    int64_t I = ((int64_t)(b[0] + i) * n + (b[1] + j)) * n + (b[2] + k);
+                    for (int r = 0; r < 3; ++r) {
+                        vp[r] += W * gv[3 * I + r];
+                        for (int c = 0; c < 3; ++c) L[3 * r + c] += gv[3 * I + r] * gW[c];
+                    }
+                }
+        double G[9];
+        for (int i = 0; i < 9; ++i) G[i] = ((i % 4 == 0) ? 1.0 : 0.0) + dt * L[i];
+        matmul3(G, F + 9 * p, F + 9 * p);
+        if (cfg->plasticity) err |= orc_von_mises(F + 9 * p, mu[p], cfg->yield_stress);
+        for (int r = 0; r < 3; ++r) {
+            v[3 * p + r] = vp[r];
+            x[3 * p + r] += dt * vp[r];
+        }
+        memcpy(C + 9 * p, L, sizeof L);
+        for (int i = 0; i < 3; ++i) if (!isfinite(x[3 * p + i]) || !isfinite(v[3 * p + i])) err |= ORC_ERR_NONFINITE;
+        for (int i = 0; i < 9; ++i) if (!isfinite(F[9 * p + i])) err |= ORC_ERR_NONFINITE;
+    }
+    return err;
+}
+
+/* One substep of the standard MPM: P2G (Eq. 1, 2), the same node loop as
+ * MLS-MPM (Eq. 3, contact, walls), G2P (Eq. 4, 5), reset, rigid advance and
+ * push-out. */
+int orc_substep_standard(const orc_config* cfg, int N, double* x, double* v, double* C, double* F,
+                         const double* mu, const double* lam, int n_rigid, orc_rigid* rigids, double dt,
+                         double* grid)
+{
+    int64_t nn = (int64_t)cfg->n * cfg->n * cfg->n;
+    memset(grid, 0, (size_t)nn * 4 * sizeof(double));
+    double* gm = grid;
+    double* gmv = grid + nn;
+    int err = orc_p2g_standard(cfg, N, x, v, F, mu, lam, dt, gm, gmv);
+    if (err & ORC_ERR_OUT_OF_DOMAIN) return err;
+    err |= orc_grid_update(cfg, gm, gmv, n_rigid, rigids, dt);
+    err |= orc_g2p_standard(cfg, N, x, v, C, F, mu, dt, gmv);
+    for (int r = 0; r < n_rigid; ++r) orc_rigid_advance(&rigids[r], dt);
+    for (int p = 0; p < N; ++p)
+        for (int r = 0; r < n_rigid; ++r) orc_push_out(&rigids[r], x + 3 * p);
+    return err;
+}
+
+/* ------------------------------------------------------------- PB-MPM */
+
+/* Co-rotational material constraint of PB-MPM (Sec. III-C), solved for one
+ * particle: F* = (I + dt C) F, R from the polar decomposition of F*,
+ * F* <- beta R + (1 - beta) F* / det(F*) (as printed), and the candidate
+ * velocity gradient C <- (F* F^-1 - I) / dt.  Cout may alias C. */
+void orc_pb_constraint(const double C[9], const double F[9], double dt, double beta, double Cout[9])
+{
+    double G[9], Fs[9], R[9], Finv[9], M[9];
+    for (int i = 0; i < 9; ++i) G[i] = ((i % 4 == 0) ? 1.0 : 0.0) + dt * C[i];
+    matmul3(G, F, Fs);
+    orc_polar_R(Fs, R);
+    double J = det3(Fs);
+    for (int i = 0; i < 9; ++i) Fs[i] = beta * R[i] + (1.0 - beta) * Fs[i] / J;
+    /* F^-1 by the adjugate */
+    double dF = det3(F);
+    Finv[0] = (F[4] * F[8] - F[5] * F[7]) / dF;
+    Finv[1] = (F[2] * F[7] - F[1] * F[8]) / dF;
+    Finv[2] = (F[1] * F[5] - F[2] * F[4]) / dF;
+    Finv[3] = (F[5] * F[6] - F[3] * F[8]) / dF;
+    Finv[4] = (F[0] * F[8] - F[2] * F[6]) / dF;
+    Finv[5] = (F[2] * F[3] - F[0] * F[5]) / dF;
+    Finv[6] = (F[3] * F[7] - F[4] * F[6]) / dF;
+    Finv[7] = (F[1] * F[6] - F[0] * F[7]) / dF;
+    Finv[8] = (F[0] * F[4] - F[1] * F[3]) / dF;
+    matmul3(Fs, Finv, M);
+    for (int i = 0; i < 9; ++i) Cout[i] = (M[i] - ((i % 4 == 0) ? 1.0 : 0.0)) / dt;
+}
+
+/* APIC P2G without a force term (the PB-MPM transfer): m_I += phi m (Eq. 1),
+ * (m v)_I += phi m (v + C (x_I - x_p)). */
+int orc_p2g_apic(const orc_config* cfg, int N, const double* x, const double* v, const double* C, double* gm,
+                 double* gmv)
+{
+    int err = 0, n = cfg->n;
+    double dx = 1.0 / n;
+    for (int p = 0; p < N; ++p) {
+        int b[3];
+        double f[3], w[3][3];
+        int e = base_and_frac(cfg, x + 3 * p, b, f);
+        if (e) { err |= e; continue; }
+        for (int d = 0; d < 3; ++d) orc_bspline_weights(f[d], w[d]);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                for (int k = 0; k < 3; ++k) {
+                    double W = w[0][i] * w[1][j] * w[2][k];
+                    double dpos[3] = {(b[0] + i) * dx - x[3 * p], (b[1] + j) * dx - x[3 * p + 1],
+                                      (b[2] + k) * dx - x[3 * p + 2]};
+                    int64_t I = ((int64_t)(b[0] + i) * n + (b[1] + j)) * n + (b[2] + k);
+                    gm[I] += W * cfg->m_p;
+                    for (int r = 0; r < 3; ++r)
+                        gmv[3 * I + r] += W * cfg->m_p * (v[3 * p + r] + C[9 * p + 3 * r] * dpos[0] +
+                                                          C[9 * p + 3 * r + 1] * dpos[1] + C[9 * p + 3 * r + 2] * dpos[2]);
+                }
+    }
+    return err;
+}
+
+/* G2P of one PB-MPM iteration: v_p = sum phi v_I (Eq. 4) and the APIC
+ * C_p = (4/dx^2) sum phi v_I (x_I - x_p)^T (Eq. 9); positions and F wait for
+ * the end of the step. */
+int orc_g2p_vc(const orc_config* cfg, int N, const double* x, double* v, double* C, const double* gv)
+{
+    int err = 0, n = cfg->n;
+    double dx = 1.0 / n, Dinv = 4.0 / (dx * dx);
+    for (int p = 0; p < N; ++p) {
+        int b[3];
+        double f[3], w[3][3];
+        int e = base_and_frac(cfg, x + 3 * p, b, f);
+        if (e) { err |= e; continue; }
+        for (int d = 0; d < 3; ++d) orc_bspline_weights(f[d], w[d]);
+        double vp[3] = {0, 0, 0}, B[9] = {0};
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                for (int k = 0; k < 3; ++k) {
+                    double W = w[0][i] * w[1][j] * w[2][k];
+                    double dpos[3] = {(b[0] + i) * dx - x[3 * p], (b[1] + j) * dx - x[3 * p + 1],
+                                      (b[2] + k) * dx - x[3 * p + 2]};
+                    int64_t I = ((int64_t)(b[0] + i) * n + (b[1] + j)) * n + (b[2] + k);
+                    for (int r = 0; r < 3; ++r) {
+                        vp[r] += W * gv[3 * I + r];
+                        for (int c = 0; c < 3; ++c) B[3 * r + c] += W * gv[3 * I + r] * dpos[c];
+                    }
+                }
+        for (int r = 0; r < 3; ++r) v[3 * p + r] = vp[r];
+        for (int i = 0; i < 9; ++i) C[9 * p + i] = Dinv * B[i];
+    }
+    return err;
+}
+
+/* One PB-MPM step (Sec. III-C): `iters` P2G-G2P cycles at fixed positions,
+ * each solving the co-rotational constraint of every particle in P2G (in
+ * place of the stress), then the APIC transfer, the node loop and the APIC
+ * G2P; then positions and F are integrated with the last velocity and
+ * velocity gradient, the rigids advance and particles are pushed out.
+ * Readings: gravity enters once per step (the first cycle's node loop; later
+ * cycles start from velocities that already hold it); contact and walls act
+ * in every cycle and every cycle's contact momentum is booked to the rigids. */
+int orc_pb_step(const orc_config* cfg, int N, double* x, double* v, double* C, double* F, int n_rigid,
+                orc_rigid* rigids, double dt, int iters, double beta, double* grid)
+{
+    int64_t nn = (int64_t)cfg->n * cfg->n * cfg->n;
+    double* gm = grid;
+    double* gmv = grid + nn;
+    int err = 0;
+    orc_config later = *cfg;
+    later.gravity[0] = later.gravity[1] = later.gravity[2] = 0.0;
+    for (int it = 0; it < iters; ++it) {
+        for (int p = 0; p < N; ++p) orc_pb_constraint(C + 9 * p, F + 9 * p, dt, beta, C + 9 * p);
+        memset(grid, 0, (size_t)nn * 4 * sizeof(double));
+        err |= orc_p2g_apic(cfg, N, x, v, C, gm, gmv);
+        if (err & ORC_ERR_OUT_OF_DOMAIN) return err;
+        err |= orc_grid_update(it == 0 ? cfg : &later, gm, gmv, n_rigid, rigids, dt);
+        err |= orc_g2p_vc(cfg, N, x, v, C, gmv);
+    }
+    for (int p = 0; p < N; ++p) {
+        double G[9];
+        for (int i = 0; i < 9; ++i) G[i] = ((i % 4 == 0) ? 1.0 : 0.0) + dt * C[9 * p + i];
+        matmul3(G, F + 9 * p, F + 9 * p);
+        for (int r = 0; r < 3; ++r) x[3 * p + r] += dt * v[3 * p + r];
+        for (int i = 0; i < 3; ++i) if (!isfinite(x[3 * p + i]) || !isfinite(v[3 * p + i])) err |= ORC_ERR_NONFINITE;
+        for (int i = 0; i < 9; ++i) if (!isfinite(F[9 * p + i])) err |= ORC_ERR_NONFINITE;
+    }
+    for (int r = 0; r < n_rigid; ++r) orc_rigid_advance(&rigids[r], dt);
+    for (int p = 0; p < N; ++p)
+        for (int r = 0; r < n_rigid; ++r) orc_push_out(&rigids[r], x + 3 * p);
+    return err;
+}
+
+/* n_steps steps of a solver: 0 MLS-MPM (orc_substep), 1 standard MPM, 2
+ * PB-MPM with `iters` cycles and stiffness beta.  Stops at the first error. */
+int orc_run_solver(const orc_config* cfg, int solver, int N, double* x, double* v, double* C, double* F,
+                   const double* mu, const double* lam, int n_rigid, orc_rigid* rigids, double dt, int n_steps,
+                   int iters, double beta)
+{
+    int64_t nn = (int64_t)cfg->n * cfg->n * cfg->n;
+    double* grid = (double*)malloc((size_t)nn * 4 * sizeof(double));
+    if (!grid) return -1;
+    int err = 0;
+    for (int s = 0; s < n_steps && !err; ++s) {
+        if (solver == 1) err = orc_substep_standard(cfg, N, x, v, C, F, mu, lam, n_rigid, rigids, dt, grid);
+        else if (solver == 2) err = orc_pb_step(cfg, N, x, v, C, F, n_rigid, rigids, dt, iters, beta, grid);
+        else err = orc_substep(cfg, N, x, v, C, F, mu, lam, n_rigid, rigids, dt, grid);
+    }
+    free(grid);
+    return err;
+}
+
 /* ------------------------------------------------------------- binning */
 
 /* Sort-by-cell: particles ordered by the 4^3-cell brick holding their base

@@ -695,3 +695,150 @@ def test_push_out_in_the_step_uses_the_moved_pose():
     c1 = c0 + dt * vel
     assert np.max(np.abs(oracle.rigid_pose(rig[0])[0] - c1)) < 1e-15
     assert np.max(np.abs(np.linalg.norm(st.x - c1, axis=1) - R)) < 1e-13
+
+
+# ------------------------------------------------------------ standard MPM
+
+def test_bspline_derivative():
+    # dN/dr of the quadratic basis (Sec. III-A: grad phi of Eq. 2 and Eq. 5)
+    # against central differences of N; the basis is C1 (the difference is
+    # O(h) only where the second derivative jumps, |r| = 0.5, 1.5).
+    for r in np.linspace(-1.6, 1.6, 161):
+        h = 1e-6
+        fd = (oracle.bspline_N(r + h) - oracle.bspline_N(r - h)) / (2 * h)
+        assert abs(oracle.bspline_dN(r) - fd) < 1e-6, r
+
+
+def test_standard_g2p_affine_grid_field():
+    # An affine grid velocity v_I = a + A x_I gives v_p = a + A x_p (Eq. 4) and
+    # L = sum v_I grad phi^T = A (Eq. 5) at any particle position: partition of
+    # unity and linear reproduction of the basis and of its gradient.
+    n, N = 32, 300
+    cfg = oracle.make_config(n, 1.0, 1e-5, gravity=(0.0, 0.0, 0.0))
+    g = np.random.default_rng(41)
+    a, A = g.normal(size=3), g.normal(size=(3, 3))
+    I = np.stack(np.meshgrid(*[np.arange(n)] * 3, indexing="ij"), -1).reshape(-1, 3) / n
+    gv = a + I @ A.T
+    x = _cloud(N, n)
+    st = oracle.State(x, mu=1.0, lam=1.0)
+    assert oracle.g2p_standard(cfg, st, gv, 0.0) == 0
+    assert np.max(np.abs(st.v - (a + x @ A.T))) < 1e-12
+    assert np.max(np.abs(st.C - A)) < 1e-11
+
+
+@pytest.mark.parametrize("model", ["fixed_corotated", "neo_hookean"])
+def test_standard_force_is_the_energy_gradient(model):
+    # The internal force of Eq. 2 is minus the gradient of the elastic energy
+    # with respect to grid-node displacements: moving node I by delta_I deforms
+    # each particle by F <- (I + sum delta_I grad phi_I^T) F (the F update of
+    # Eq. 5 with v_I = delta_I / dt), and the P2G momentum of particles at rest
+    # is dt f^int.  Central differences of the energy over a few nodes.
+    n, N, dt = 16, 40, 1e-3
+    V0, mu, lam = 2e-4, 30.0, 50.0
+    cfg = oracle.make_config(n, 1.0, V0, model=model, gravity=(0.0, 0.0, 0.0))
+    g = np.random.default_rng(42)
+    x = _cloud(N, n, 0.4, 0.6)
+    F0 = np.eye(3) + 0.1 * g.normal(size=(N, 3, 3))
+    st = oracle.State(x, F=F0, mu=mu, lam=lam)
+    gm, gmv, err = oracle.p2g_standard(cfg, st, dt)
+    assert err == 0
+
+    def energy(delta):
+        s = oracle.State(x, F=F0, mu=mu, lam=lam)
+        assert oracle.g2p_standard(cfg, s, delta / dt, dt) == 0
+        return sum(V0 * _energy(model, Fp, mu, lam) for Fp in s.F)
+
+    nodes = np.flatnonzero(gm)[:: max(1, len(np.flatnonzero(gm)) // 12)]
+    h = 1e-7
+    for I in nodes:
+        for r in range(3):
+            d = np.zeros((n ** 3, 3))
+            d[I, r] = h
+            fd = -(energy(d) - energy(-d)) / (2 * h)
+            assert abs(gmv[I, r] / dt - fd) <= 1e-6 * max(1.0, abs(fd)), (I, r, gmv[I, r] / dt, fd)
+
+
+def test_standard_free_fall_and_momentum():
+    # Uniform velocity at rest shape: no force, the step adds dt g (Eq. 3, 4);
+    # with no gravity, walls or rigids, a deformed block keeps its momentum.
+    n, N, dt = 32, 300, 1e-3
+    cfg = oracle.make_config(n, 1.0, 1e-5)
+    v0 = np.array([0.2, 0.1, -0.3])
+    st = oracle.State(_cloud(N, n, 0.4, 0.6), np.tile(v0, (N, 1)), mu=10.0, lam=10.0)
+    x0 = st.x.copy()
+    assert oracle.run_solver(cfg, st, dt, 1, "standard") == 0
+    gvec = np.array(cfg.gravity[:])
+    assert np.max(np.abs(st.v - (v0 + dt * gvec))) < 1e-12
+    assert np.max(np.abs(st.x - (x0 + dt * (v0 + dt * gvec)))) < 1e-14
+    cfg0 = oracle.make_config(n, 0.7, 1e-4, gravity=(0.0, 0.0, 0.0))
+    g = np.random.default_rng(43)
+    st = oracle.State(_cloud(N, n), g.normal(size=(N, 3)), F=np.eye(3) + 0.05 * g.normal(size=(N, 3, 3)),
+                      mu=40.0, lam=60.0)
+    P0 = st.v.sum(0)
+    assert oracle.run_solver(cfg0, st, 2e-4, 3, "standard") == 0
+    assert rel(st.v.sum(0), P0) < 1e-11
+
+
+# ------------------------------------------------------------------ PB-MPM
+
+def test_pb_constraint_limits():
+    # Sec. III-C co-rotational constraint: with beta = 1 the corrected
+    # deformation (I + dt C') F is the polar rotation of (I + dt C) F; with
+    # beta = 0 it is (I + dt C) F / det((I + dt C) F); in between it is their
+    # blend, so C' is affine in beta.
+    from scipy.linalg import polar
+
+    g = np.random.default_rng(44)
+    dt = 0.02
+    for _ in range(30):
+        C = g.normal(size=(3, 3))
+        F = np.eye(3) + 0.2 * g.normal(size=(3, 3))
+        Fh = (np.eye(3) + dt * C) @ F
+        if np.linalg.det(Fh) <= 0.1 or np.linalg.det(F) <= 0.1:
+            continue
+        R, _ = polar(Fh)
+        c1 = oracle.pb_constraint(C, F, dt, 1.0)
+        c0 = oracle.pb_constraint(C, F, dt, 0.0)
+        assert np.max(np.abs((np.eye(3) + dt * c1) @ F - R)) < 1e-12
+        assert np.max(np.abs((np.eye(3) + dt * c0) @ F - Fh / np.linalg.det(Fh))) < 1e-12
+        b = g.uniform()
+        assert np.max(np.abs(oracle.pb_constraint(C, F, dt, b) - (b * c1 + (1 - b) * c0))) < 1e-10
+
+
+def test_pb_single_particle_step_closed_form():
+    # One particle, no gravity, walls or rigids: the grid field of an APIC
+    # transfer from a single particle is affine around it, so every G2P returns
+    # the particle's velocity and the C the constraint produced (Eq. 8, 9).
+    # With beta = 1 the constraint is idempotent, hence after any number of
+    # cycles F_new = polar rotation of (I + dt C0) F and x moves by dt v.
+    from scipy.linalg import polar
+
+    n, dt = 32, 0.02
+    cfg = oracle.make_config(n, 1.0, 1e-5, gravity=(0.0, 0.0, 0.0))
+    g = np.random.default_rng(45)
+    for iters in (1, 3, 10):
+        C0, F0 = 2.0 * g.normal(size=(3, 3)), np.eye(3) + 0.1 * g.normal(size=(3, 3))
+        v0, x0 = g.normal(size=3) * 0.1, np.array([0.47, 0.52, 0.49])
+        st = oracle.State(x0[None], v0[None], C0[None], F0[None], mu=1.0, lam=1.0)
+        assert oracle.run_solver(cfg, st, dt, 1, "pb", iters=iters, beta=1.0) == 0
+        R, _ = polar((np.eye(3) + dt * C0) @ F0)
+        assert np.max(np.abs(st.F[0] - R)) < 1e-11
+        assert np.max(np.abs(st.v[0] - v0)) < 1e-13
+        assert np.max(np.abs(st.x[0] - (x0 + dt * v0))) < 1e-14
+
+
+def test_pb_gravity_enters_once_per_step():
+    # At rest shape (F = I, C = 0) the constraint changes nothing, so a falling
+    # cloud gains dt g per step whatever the number of cycles (reading: gravity
+    # in the first cycle's node loop only).
+    n, N, dt = 32, 200, 0.02
+    cfg = oracle.make_config(n, 1.0, 1e-5)
+    v0 = np.array([0.1, 0.0, -0.05])
+    gvec = np.array(cfg.gravity[:])
+    for iters in (1, 5):
+        st = oracle.State(_cloud(N, n, 0.45, 0.55), np.tile(v0, (N, 1)), mu=1.0, lam=1.0)
+        x0 = st.x.copy()
+        assert oracle.run_solver(cfg, st, dt, 1, "pb", iters=iters, beta=0.5) == 0
+        assert np.max(np.abs(st.v - (v0 + dt * gvec))) < 1e-12
+        assert np.max(np.abs(st.x - (x0 + dt * (v0 + dt * gvec)))) < 1e-13
+        assert np.max(np.abs(st.F - np.eye(3))) < 1e-12
