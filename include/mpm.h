@@ -64,6 +64,15 @@ extern "C" {
 enum { MPM_MEM_HOST = 0, MPM_MEM_DEVICE = 1 };
 enum { MPM_FIXED_COROTATED = 0, MPM_NEO_HOOKEAN = 1 };
 enum { MPM_PLASTIC_NONE = 0, MPM_PLASTIC_VON_MISES = 1 };
+/* Solvers (Sec. III).  MLS: APIC-style MLS-MPM, Algorithm 1 (Sec. III-B).
+ * STANDARD: PIC transfers with the internal force -V sigma grad phi (Eq. 1-6,
+ * Sec. III-A); C then holds the velocity gradient L of the F update.
+ * PB: position-based MPM (Sec. III-C): each substep runs pb_iterations cycles
+ * of the co-rotational constraint in P2G, the APIC transfers and the grid
+ * update at fixed positions, then integrates x and F; gravity enters once per
+ * substep, contact and walls act in every cycle (their momentum is booked to
+ * the rigids in every cycle), plasticity and mpm_backward are not available. */
+enum { MPM_SOLVER_MLS = 0, MPM_SOLVER_STANDARD = 1, MPM_SOLVER_PB = 2 };
 enum { MPM_SPHERE = 0, MPM_BOX = 1, MPM_QUAD_SLICER = 2, MPM_SEGMENTS = 3, MPM_RIGID_NONE = -1 };
 
 #define MPM_MAX_SEGMENT_POINTS 64
@@ -118,7 +127,12 @@ typedef struct {
     int32_t tape_checkpoint_every; /* > 0 enables mpm_tape_begin/mpm_backward; the
                                       tape stores a checkpoint every this many substeps */
     int32_t tape_max_substeps;   /* longest recordable tape (substeps)               */
-    int32_t reserved[7];         /* zero */
+    int32_t solver;              /* MPM_SOLVER_MLS (0, default), MPM_SOLVER_STANDARD or
+                                    MPM_SOLVER_PB (Sec. III: the paper's three solvers) */
+    int32_t pb_iterations;       /* PB-MPM: P2G-G2P cycles per step (0: 10)           */
+    float pb_beta;               /* PB-MPM: blend beta in [0,1] of the co-rotational
+                                    constraint (1: rotation only, stiffest)          */
+    int32_t reserved[4];         /* zero */
 } mpm_config;
 
 /* A rigid body (Sec. IV).  Body frame -> world frame by the unit quaternion

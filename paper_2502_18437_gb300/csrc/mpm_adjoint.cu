@@ -79,14 +79,6 @@ struct AdjArgs {
     float* glam;
 };
 
-// Derivatives of the three quadratic B-spline weights with respect to f.
-__device__ __forceinline__ void bspline_d(float f, float dw[3])
-{
-    dw[0] = f - 1.5f;
-    dw[1] = -2.0f * (f - 1.0f);
-    dw[2] = f - 0.5f;
-}
-
 __device__ __forceinline__ int scene_of(const StepArgs& a, int i)
 {
     int lo = a.r.s0, hi = a.r.s1 - 1;
@@ -598,7 +590,7 @@ extern "C" int mpm_tape_begin(mpm_ctx* c)
 {
     if (!c) return MPM_ERR_INVALID_ARGUMENT;
     if (c->cfg.tape_checkpoint_every <= 0 || c->cfg.tape_max_substeps <= 0) return MPM_ERR_STATE;
-    if (c->cfg.plasticity != MPM_PLASTIC_NONE) return MPM_ERR_STATE;
+    if (c->cfg.plasticity != MPM_PLASTIC_NONE || c->cfg.solver != MPM_SOLVER_MLS) return MPM_ERR_STATE;
     int st = upload_scenes(c);
     if (st) return st;
     if ((st = ensure_keys(c))) return st;

@@ -171,6 +171,12 @@ StepArgs step_args(mpm_ctx* c, float dt, int s0, int s1, const PState& in, const
     a.p2g_chunk = c->p2g_chunk;
     a.g2p_threads = c->g2p_threads;
     a.cell_order = 1;
+    a.solver = c->cfg.solver;
+    a.pb_beta = c->cfg.pb_beta;
+    if (a.solver == MPM_SOLVER_STANDARD) {
+        if (!c->occ_p2g_std) c->occ_p2g_std = std::max(1, occupancy_p2g_std());
+        a.p2g_ctas = c->num_sms * c->occ_p2g_std;
+    }
     a.any_rigid = 0;
     for (int sc = s0; sc < s1; ++sc)
         if (c->h_scenes[sc].n_rigid > 0) a.any_rigid = 1;
@@ -204,7 +210,34 @@ int enqueue_substep(mpm_ctx* c, float dt, const PState& in, const PState& out, b
         if (ev) MPM_CK(cudaEventRecord(ev[0], c->stream));
         MPM_CK(launch_sort(a, c->stream));
         if (ev) MPM_CK(cudaEventRecord(ev[1], c->stream));
-        if (!c->fused || need_p2g) MPM_CK(launch_p2g(a, c->stream));
+        if (a.solver == MPM_SOLVER_PB) {
+            // PB-MPM: cycles of constraint + P2G, grid update and G2P of v and C at
+            // fixed positions (the sort above serves them all); gravity in the first
+            // cycle only; the last cycle's G2P integrates x and F and ends the substep
+            const int cycles = c->cfg.pb_iterations > 0 ? c->cfg.pb_iterations : 10;
+            for (int k = 0; k < cycles; ++k) {
+                StepArgs b = a;
+                if (k > 0) {
+                    for (int d = 0; d < 3; ++d) b.gravity[d] = 0.f;
+                    b.cell_order = 0;  // the first P2G left the permutation in cell order
+                    MPM_CK(cudaMemsetAsync(c->sb.counters + CTR_WORK_P2G, 0, sizeof(int) * 3, c->stream));
+                }
+                MPM_CK(launch_p2g(b, c->stream));
+                MPM_CK(launch_grid(b, c->stream));
+                if (k + 1 < cycles) MPM_CK(launch_g2p_vc(b, c->stream));
+                else {
+                    if (ev) MPM_CK(cudaEventRecord(ev[2], c->stream));
+                    if (ev) MPM_CK(cudaEventRecord(ev[3], c->stream));
+                    MPM_CK(launch_g2p(b, c->stream));
+                }
+            }
+            if (ev) MPM_CK(cudaEventRecord(ev[4], c->stream));
+            continue;
+        }
+        if (!c->fused || need_p2g) {
+            if (a.solver == MPM_SOLVER_STANDARD) MPM_CK(launch_p2g_std(a, c->stream));
+            else MPM_CK(launch_p2g(a, c->stream));
+        }
         if (ev) MPM_CK(cudaEventRecord(ev[2], c->stream));
         MPM_CK(launch_grid(a, c->stream));
         if (ev) MPM_CK(cudaEventRecord(ev[3], c->stream));
@@ -212,8 +245,9 @@ int enqueue_substep(mpm_ctx* c, float dt, const PState& in, const PState& out, b
         else MPM_CK(launch_g2p(a, c->stream));
         if (ev) MPM_CK(cudaEventRecord(ev[4], c->stream));
     }
-    // the unfused G2P stores the new stress; the fused kernel keeps it in registers
-    c->tau_valid = !c->fused;
+    // the unfused G2P stores the new stress; the fused kernel keeps it in registers;
+    // PB-MPM stores none
+    c->tau_valid = !c->fused && c->cfg.solver != MPM_SOLVER_PB;
     return MPM_OK;
 }
 
@@ -295,6 +329,11 @@ extern "C" int mpm_create(const mpm_config* cfg, void* stream, mpm_ctx** out)
     if (cfg->model != MPM_FIXED_COROTATED && cfg->model != MPM_NEO_HOOKEAN) return MPM_ERR_INVALID_ARGUMENT;
     if (cfg->plasticity != MPM_PLASTIC_NONE && cfg->plasticity != MPM_PLASTIC_VON_MISES) return MPM_ERR_INVALID_ARGUMENT;
     if (cfg->bound < 0) return MPM_ERR_INVALID_ARGUMENT;
+    if (cfg->solver < MPM_SOLVER_MLS || cfg->solver > MPM_SOLVER_PB) return MPM_ERR_INVALID_ARGUMENT;
+    if (cfg->solver == MPM_SOLVER_PB &&
+        (cfg->pb_iterations < 0 || cfg->pb_iterations > 1000 || !(cfg->pb_beta >= 0.f && cfg->pb_beta <= 1.f) ||
+         cfg->plasticity != MPM_PLASTIC_NONE))
+        return MPM_ERR_INVALID_ARGUMENT;
     mpm_ctx* c = new mpm_ctx();
     c->cfg = *cfg;
     c->cfg.scene_grid_n = nullptr;
@@ -468,6 +507,7 @@ extern "C" int mpm_set_option(mpm_ctx* c, int option, int64_t value)
     case MPM_OPT_PHASE_TIMING: c->phase_timing = value != 0; break;
     case MPM_OPT_G2P_REGS64: c->g2p_regs64 = value != 0; break;
     case MPM_OPT_FUSED:
+        if (value != 0 && c->cfg.solver != MPM_SOLVER_MLS) return MPM_ERR_INVALID_ARGUMENT;
         c->fused = value != 0;
         invalidate_pending(c);
         break;

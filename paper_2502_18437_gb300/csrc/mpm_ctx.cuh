@@ -69,6 +69,7 @@ struct mpm_ctx {
     int occ_p2g[3] = {};
     int occ_grid = 0;
     int occ_fused = 0;
+    int occ_p2g_std = 0;
     std::vector<cudaEvent_t> phase_events;  // 5 per timed substep
     size_t phase_used = 0;
     std::map<std::tuple<uint32_t, int, int>, cudaGraphExec_t> graphs;

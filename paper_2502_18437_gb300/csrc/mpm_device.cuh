@@ -115,6 +115,15 @@ __device__ __forceinline__ void bspline(float f, float w[3])
     w[2] = 0.5f * c * c;
 }
 
+// Derivatives of the three quadratic B-spline weights with respect to f
+// (the basis gradient of the standard MPM's Eq. 2 and Eq. 5 is n times these).
+__device__ __forceinline__ void bspline_d(float f, float dw[3])
+{
+    dw[0] = f - 1.5f;
+    dw[1] = -2.0f * (f - 1.0f);
+    dw[2] = f - 0.5f;
+}
+
 __device__ __forceinline__ float det3(const float F[9])
 {
     return F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
@@ -367,6 +376,54 @@ __device__ __forceinline__ unsigned constitutive(int model, int plastic, float y
     t6[4] = mu * (F[3] * F[6] + F[4] * F[7] + F[5] * F[8]);
     t6[5] = mu * (F[6] * F[6] + F[7] * F[7] + F[8] * F[8]) + d;
     return e;
+}
+
+// Co-rotational material constraint of PB-MPM (Sec. III-C) for one particle,
+// in place of the stress in P2G: F* = (I + dt C) F, R its polar rotation,
+// F* <- beta R + (1 - beta) F* / det(F*) (as printed), C <- (F* F^-1 - I) / dt.
+// R = U diag(s)^-1 U^T F* from the left stretch of F* (F* = U diag(s) V^T with
+// U, V rotations, so R = U V^T).
+__device__ __forceinline__ void pb_constraint(const float F[9], float dt, float beta, float C[9])
+{
+    float Fh[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            Fh[3 * r + c] = F[3 * r + c] + dt * (C[3 * r] * F[c] + C[3 * r + 1] * F[3 + c] + C[3 * r + 2] * F[6 + c]);
+    float U[9], s[3];
+    left_stretch(Fh, U, s);
+    const float i0 = 1.0f / s[0], i1 = 1.0f / s[1], i2 = 1.0f / s[2];
+    float M[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = r; c < 3; ++c) {
+            M[3 * r + c] = U[3 * r] * i0 * U[3 * c] + U[3 * r + 1] * i1 * U[3 * c + 1] + U[3 * r + 2] * i2 * U[3 * c + 2];
+            M[3 * c + r] = M[3 * r + c];
+        }
+    const float k = (1.0f - beta) / det3(Fh);
+    float Fs[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            Fs[3 * r + c] = beta * (M[3 * r] * Fh[c] + M[3 * r + 1] * Fh[3 + c] + M[3 * r + 2] * Fh[6 + c]) +
+                            k * Fh[3 * r + c];
+    // F^-1 = adj(F) / det(F)
+    const float id = 1.0f / det3(F);
+    const float Fi[9] = {(F[4] * F[8] - F[5] * F[7]) * id, (F[2] * F[7] - F[1] * F[8]) * id,
+                         (F[1] * F[5] - F[2] * F[4]) * id, (F[5] * F[6] - F[3] * F[8]) * id,
+                         (F[0] * F[8] - F[2] * F[6]) * id, (F[2] * F[3] - F[0] * F[5]) * id,
+                         (F[3] * F[7] - F[4] * F[6]) * id, (F[1] * F[6] - F[0] * F[7]) * id,
+                         (F[0] * F[4] - F[1] * F[3]) * id};
+    const float idt = 1.0f / dt;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            C[3 * r + c] = ((Fs[3 * r] * Fi[c] + Fs[3 * r + 1] * Fi[3 + c] + Fs[3 * r + 2] * Fi[6 + c]) -
+                            (r == c ? 1.0f : 0.0f)) * idt;
 }
 
 // Rotation matrix of the unit quaternion (w, x, y, z).

@@ -277,7 +277,12 @@ constexpr int kSliceNodes = 4 * 36;  // node planes x = slice .. slice + 3 of th
 constexpr int kStageFloats = 36 * 3 * 64;  // (9 nodes x 4 values) x 3 slices x 64 items
 constexpr int kWinFloats = 3 * 4 * kSliceNodes;  // the slices' windows, after the stage
 
-template <int PER>
+// MODE: kP2GStress (MLS-MPM: the Kirchhoff stress, stored by G2P or computed
+// from F) or kP2GConstraint (PB-MPM: the co-rotational constraint replaces C
+// and there is no stress term).
+enum { kP2GStress = 0, kP2GConstraint = 1 };
+
+template <int PER, int MODE>
 __global__ void __launch_bounds__(kP2GThreads, 4) k_p2g(StepArgs a)
 {
     constexpr int CHUNK = PER * kP2GThreads;
@@ -382,7 +387,14 @@ __global__ void __launch_bounds__(kP2GThreads, 4) k_p2g(StepArgs a)
                 for (int q = 0; q < 9; ++q) C[q] = a.in.C[(size_t)q * cap + p];
 #pragma unroll
                 for (int q = 0; q < 3; ++q) v[q] = a.in.v[(size_t)q * cap + p];
-                if (a.tau_valid) {
+                if (MODE == kP2GConstraint) {
+                    float F[9];
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) F[q] = a.in.F[(size_t)q * cap + p];
+                    pb_constraint(F, a.dt, a.pb_beta, C);
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) t6[q] = 0.f;
+                } else if (a.tau_valid) {
 #pragma unroll
                     for (int q = 0; q < 6; ++q) t6[q] = a.in.tau[(size_t)q * cap + p];
                 } else {
@@ -812,8 +824,16 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // sX[d * stride] and sF[q * stride] by cp.async one particle ahead; this call
 // starts the copies of particle pnext (when >= 0) as soon as its own values
 // are out of the buffers: x after the gather, F after the F update.
+// Variants of the forward G2P (template flags).
+enum {
+    kG2PSolids = 1,    // push particles out of solid rigids (some scene has a rigid)
+    kG2PStdGrad = 2,   // standard MPM: L = sum v_I grad phi^T instead of the APIC C (Eq. 5)
+    kG2PNoStress = 4   // PB-MPM: no constitutive update (no stress is stored)
+};
+
 // The new position is returned in o.x and stored by the caller, after the
 // particle push-out (finish_position).
+template <int FLAGS>
 __device__ __forceinline__ unsigned g2p_particle(const StepArgs& a, const SceneDev& sc, const float4* lin, int p, int s,
                                                  int ox, int oy, int oz, G2POut& o, float* sX = nullptr,
                                                  float* sF = nullptr, int stride = 0, int pnext = -1)
@@ -834,11 +854,18 @@ __device__ __forceinline__ unsigned g2p_particle(const StepArgs& a, const SceneD
     const float* wy = w + 3;
     const float* wz = w + 6;
     float wxd[3], wyd[3], wzd[3];
+    if (FLAGS & kG2PStdGrad) {
+        // the basis gradient in cell units (times n below): L_rc = n sum v_r dW/df_c
+        bspline_d(f[0], wxd);
+        bspline_d(f[1], wyd);
+        bspline_d(f[2], wzd);
+    } else {
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        wxd[q] = wx[q] * ((float)q - f[0]);
-        wyd[q] = wy[q] * ((float)q - f[1]);
-        wzd[q] = wz[q] * ((float)q - f[2]);
+        for (int q = 0; q < 3; ++q) {
+            wxd[q] = wx[q] * ((float)q - f[0]);
+            wyd[q] = wy[q] * ((float)q - f[1]);
+            wzd[q] = wz[q] * ((float)q - f[2]);
+        }
     }
     const float4* base = lin + (l0 * 36 + l1 * 6 + l2);
     float A[3][3], Ay[3][3], Bz[3][3];  // [i][component]
@@ -873,8 +900,9 @@ __device__ __forceinline__ unsigned g2p_particle(const StepArgs& a, const SceneD
 #pragma unroll
         for (int d = 0; d < 3; ++d) cp_async4(sX + d * stride, a.in.x + (size_t)d * cap + pnext);
     }
-    // C = D^-1 sum N v (x_I - x_p)^T = 4/dx^2 * dx * B  (Eq. 9); x += dt v (Eq. 4)
-    const float c4 = 4.0f * fn;
+    // C = D^-1 sum N v (x_I - x_p)^T = 4/dx^2 * dx * B  (Eq. 9), or for the
+    // standard MPM L = n B with the derivative weights (Eq. 5); x += dt v (Eq. 4)
+    const float c4 = (FLAGS & kG2PStdGrad) ? fn : 4.0f * fn;
 #pragma unroll
     for (int i = 0; i < 9; ++i) o.C[i] = B[i] * c4;
     o.v[0] = v0; o.v[1] = v1; o.v[2] = v2;
@@ -913,7 +941,7 @@ __device__ __forceinline__ unsigned g2p_particle(const StepArgs& a, const SceneD
 #pragma unroll
         for (int q = 0; q < 9; ++q) cp_async4(sF + q * stride, a.in.F + (size_t)q * cap + pnext);
     }
-    ebits |= constitutive(a.model, a.plasticity, a.yield_stress, mu, lam, Fn, o.t6);
+    if (!(FLAGS & kG2PNoStress)) ebits |= constitutive(a.model, a.plasticity, a.yield_stress, mu, lam, Fn, o.t6);
 #pragma unroll
     for (int i = 0; i < 9; ++i) a.out.F[(size_t)i * cap + s] = Fn[i];
     float chk = x0 + x1 + x2 + v0 + v1 + v2;
@@ -948,9 +976,10 @@ __device__ __forceinline__ void linearize_window(const float4* vw, float4* lin)
 // 1024/BLOCK: 64 registers, more warps in flight).  SOLIDS: some scene of the
 // launch has a rigid, so particles may need the push-out (a separate variant:
 // its extra live registers would make the 64-register build spill).
-template <int BLOCK, int MINB, bool SOLIDS>
+template <int BLOCK, int MINB, int FLAGS>
 __global__ void __launch_bounds__(BLOCK, MINB) k_g2p(StepArgs a)
 {
+    constexpr bool SOLIDS = (FLAGS & kG2PSolids) != 0;
     // x and F of each thread's next particle, copied by cp.async one particle ahead
     __shared__ float sX[3 * BLOCK], sF[9 * BLOCK];
     __shared__ __align__(128) float4 vw[2][8 * 64];
@@ -998,10 +1027,12 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_g2p(StepArgs a)
             if (valid) {
                 G2POut o;
                 const int pnext = k + BLOCK < count ? a.sb.perm[start + k + BLOCK] : -1;
-                ebits |= g2p_particle(a, sc, lin, pcur, start + k, ox, oy, oz, o, &sX[tid], &sF[tid], BLOCK, pnext);
+                ebits |= g2p_particle<FLAGS>(a, sc, lin, pcur, start + k, ox, oy, oz, o, &sX[tid], &sF[tid], BLOCK,
+                                             pnext);
                 pcur = pnext;
+                if (!(FLAGS & kG2PNoStress))
 #pragma unroll
-                for (int q = 0; q < 6; ++q) a.out.tau[(size_t)q * a.cap + start + k] = o.t6[q];
+                    for (int q = 0; q < 6; ++q) a.out.tau[(size_t)q * a.cap + start + k] = o.t6[q];
                 finish_position(a, SOLIDS ? s_pose : nullptr, n_solid, start + k, o.x);
                 unsigned ood = 0;
                 key = cell_key(sc, o.x[0], o.x[1], o.x[2], ood);
@@ -1079,7 +1110,7 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_g2p2g(StepArgs a)
             int key = 0, my_cell = -1, my_rank = 0;
             if (valid) {
                 G2POut o;
-                ebits |= g2p_particle(a, sc, lin, a.sb.perm[start + k], start + k, ox, oy, oz, o);
+                ebits |= g2p_particle<0>(a, sc, lin, a.sb.perm[start + k], start + k, ox, oy, oz, o);
                 finish_position(a, s_pose, n_solid, start + k, o.x);
                 // P2G of the next substep at the new position
                 int bc[3];
@@ -1167,6 +1198,159 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_g2p2g(StepArgs a)
         buf ^= 1;
     }
     walker_exit(a);
+}
+
+// ------------------------------------------------------- standard MPM P2G
+//
+// P2G of the standard MPM (Sec. III-A): m_I += W m (Eq. 1), and the momentum
+// W m v plus the internal-force impulse -dt V0 tau grad W (Eq. 2, 3; V sigma =
+// V0 tau).  One CTA per active particle brick accumulates its 6^3 window with
+// shared-memory float atomics and adds it to HBM with one vector reduction per
+// node.  The paper keeps this solver as a reference with fewer features; so
+// does this kernel (no per-cell work items).
+
+constexpr int kStdThreads = 256;
+
+__global__ void __launch_bounds__(kStdThreads) k_p2g_std(StepArgs a)
+{
+    __shared__ float win[4][kWinNodes];
+    __shared__ int s_item;
+    const int tid = threadIdx.x;
+    const int n_act = a.sb.counters[CTR_N_ACT];
+    const int cap = a.cap;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(&a.sb.counters[CTR_WORK_P2G], 1);
+        for (int t = tid; t < 4 * kWinNodes; t += kStdThreads) (&win[0][0])[t] = 0.0f;
+        __syncthreads();
+        const int item = s_item;
+        if (item >= n_act) break;
+        const int b = a.sb.act_brick[item], start = a.sb.act_start[item], count = a.sb.act_count[item];
+        const int scene = a.sb.act_scene[item];
+        const SceneDev sc = a.scenes[scene];
+        const int n = sc.n, nb = sc.nb, lb = b - sc.brick_base;
+        const int ox = (lb / (nb * nb)) * 4, oy = ((lb / nb) % nb) * 4, oz = (lb % nb) * 4;
+        const float fn = (float)n, m = sc.m_p;
+        const float kap = a.dt * sc.V0 * fn;  // dt V0 times the n of grad W = n dW/df
+        unsigned ebits = 0;
+        for (int k = tid; k < count; k += kStdThreads) {
+            const int p = a.sb.perm[start + k];
+            int bc[3];
+            float f[3], w[9], dw[9];
+            ebits |= particle_weights(a.in.x[p], a.in.x[cap + p], a.in.x[2 * cap + p], n, bc, f, w);
+            bspline_d(f[0], dw);
+            bspline_d(f[1], dw + 3);
+            bspline_d(f[2], dw + 6);
+            float t6[6], v[3];
+            if (a.tau_valid) {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) t6[q] = a.in.tau[(size_t)q * cap + p];
+            } else {
+                float F[9];
+#pragma unroll
+                for (int q = 0; q < 9; ++q) F[q] = a.in.F[(size_t)q * cap + p];
+                const float mu = sc.pp_mat ? a.in.mu[p] : sc.mu, lam = sc.pp_mat ? a.in.lam[p] : sc.lam;
+                ebits |= constitutive(a.model, 0, 0.f, mu, lam, F, t6);
+            }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) v[q] = m * a.in.v[(size_t)q * cap + p];
+            const float tau[9] = {t6[0], t6[1], t6[2], t6[1], t6[3], t6[4], t6[2], t6[4], t6[5]};
+            const int l0 = min(max(bc[0] - ox, 0), 3), l1 = min(max(bc[1] - oy, 0), 3), l2 = min(max(bc[2] - oz, 0), 3);
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+#pragma unroll
+                    for (int kk = 0; kk < 3; ++kk) {
+                        const float W = w[i] * w[3 + j] * w[6 + kk];
+                        const float g0 = dw[i] * w[3 + j] * w[6 + kk], g1 = w[i] * dw[3 + j] * w[6 + kk],
+                                    g2 = w[i] * w[3 + j] * dw[6 + kk];
+                        const int node = (l0 + i) * 36 + (l1 + j) * 6 + (l2 + kk);
+                        atomicAdd(&win[0][node], W * m);
+#pragma unroll
+                        for (int r = 0; r < 3; ++r)
+                            atomicAdd(&win[1 + r][node],
+                                      W * v[r] - kap * (tau[3 * r] * g0 + tau[3 * r + 1] * g1 + tau[3 * r + 2] * g2));
+                    }
+        }
+        __syncthreads();
+        for (int q = tid; q < kWinNodes; q += kStdThreads) {
+            const float mm = win[0][q];
+            if (mm == 0.0f) continue;
+            const int gi = ox + q / 36, gj = oy + (q / 6) % 6, gk = oz + q % 6;
+            if (gi >= n || gj >= n || gk >= n) continue;
+            red_add_v4(&a.G[node_index(sc, gi, gj, gk)], mm, win[1][q], win[2][q], win[3][q]);
+        }
+        if (ebits) atomicOr(&a.err[scene], ebits);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------- PB-MPM cycle G2P
+//
+// G2P of a PB-MPM cycle (Sec. III-C): positions and F stay fixed during the
+// cycles, so each particle's v = sum W v_I and APIC C = 4/dx^2 sum W v_I
+// (x_I - x_p)^T are written back in place (storage order), where the next
+// cycle's P2G reads them through the same permutation.
+
+constexpr int kVcThreads = 128;
+
+__global__ void __launch_bounds__(kVcThreads) k_g2p_vc(StepArgs a)
+{
+    __shared__ __align__(128) float4 vw[2][8 * 64];
+    __shared__ __align__(16) float4 lin[kWinNodes];
+    __shared__ __align__(8) unsigned long long bar[2];
+    __shared__ int s_item[2];
+    const int tid = threadIdx.x;
+    const int n_act = a.sb.counters[CTR_N_ACT];
+    const int cap = a.cap;
+    int* work = &a.sb.counters[CTR_WORK_G2P];
+    walker_init<kVcThreads>(a, n_act, vw, bar, s_item, work);
+    unsigned phase[2] = {0u, 0u};
+    int buf = 0;
+    for (;;) {
+        const int item = s_item[buf];
+        if (item >= n_act) break;
+        if (!walker_next(a, n_act, vw, bar, s_item, work, buf, phase, item)) break;
+        const int start = a.sb.act_start[item], count = a.sb.act_count[item];
+        const SceneDev sc = a.scenes[a.sb.act_scene[item]];
+        const int n = sc.n, nb = sc.nb, lb = a.sb.act_brick[item] - sc.brick_base;
+        const int ox = (lb / (nb * nb)) * 4, oy = ((lb / nb) % nb) * 4, oz = (lb % nb) * 4;
+        const float c4 = 4.0f * (float)n;
+        linearize_window<kVcThreads>(vw[buf], lin);
+        __syncthreads();
+        for (int k = tid; k < count; k += kVcThreads) {
+            const int p = a.sb.perm[start + k];
+            int bc[3];
+            float f[3], w[9];
+            particle_weights(a.in.x[p], a.in.x[cap + p], a.in.x[2 * cap + p], n, bc, f, w);
+            const int l0 = min(max(bc[0] - ox, 0), 3), l1 = min(max(bc[1] - oy, 0), 3), l2 = min(max(bc[2] - oz, 0), 3);
+            float vv[3] = {0.f, 0.f, 0.f}, B[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+#pragma unroll
+                    for (int kk = 0; kk < 3; ++kk) {
+                        const float W = w[i] * w[3 + j] * w[6 + kk];
+                        const float4 g = lin[(l0 + i) * 36 + (l1 + j) * 6 + (l2 + kk)];
+                        const float d0 = (float)i - f[0], d1 = (float)j - f[1], d2 = (float)kk - f[2];
+                        const float gv[3] = {g.x, g.y, g.z};
+#pragma unroll
+                        for (int r = 0; r < 3; ++r) {
+                            vv[r] += W * gv[r];
+                            B[3 * r] += W * gv[r] * d0;
+                            B[3 * r + 1] += W * gv[r] * d1;
+                            B[3 * r + 2] += W * gv[r] * d2;
+                        }
+                    }
+#pragma unroll
+            for (int r = 0; r < 3; ++r) a.in.v[(size_t)r * cap + p] = vv[r];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) a.in.C[(size_t)q * cap + p] = c4 * B[q];
+        }
+        __syncthreads();
+        buf ^= 1;
+    }
 }
 
 // ------------------------------------------------------- state I/O kernels
@@ -1259,22 +1443,51 @@ static constexpr size_t p2g_dyn_smem() { return sizeof(float) * kItemRecFields *
 
 cudaError_t prepare_p2g()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_p2g<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2g_dyn_smem<2>());
+    cudaError_t e = cudaFuncSetAttribute(k_p2g<2, kP2GStress>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)p2g_dyn_smem<2>());
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_p2g<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2g_dyn_smem<3>());
+        e = cudaFuncSetAttribute(k_p2g<3, kP2GStress>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)p2g_dyn_smem<3>());
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_p2g<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2g_dyn_smem<4>());
+        e = cudaFuncSetAttribute(k_p2g<4, kP2GStress>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)p2g_dyn_smem<4>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_p2g<4, kP2GConstraint>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)p2g_dyn_smem<4>());
     return e;
 }
 
 cudaError_t launch_p2g(const StepArgs& a, cudaStream_t s)
 {
+    if (a.solver == MPM_SOLVER_PB) {
+        k_p2g<4, kP2GConstraint><<<a.p2g_ctas, kP2GThreads, p2g_dyn_smem<4>(), s>>>(a);
+        return cudaGetLastError();
+    }
     switch (a.p2g_chunk) {
-    case 2 * kP2GThreads: k_p2g<2><<<a.p2g_ctas, kP2GThreads, p2g_dyn_smem<2>(), s>>>(a); break;
-    case 4 * kP2GThreads: k_p2g<4><<<a.p2g_ctas, kP2GThreads, p2g_dyn_smem<4>(), s>>>(a); break;
-    default: k_p2g<3><<<a.p2g_ctas, kP2GThreads, p2g_dyn_smem<3>(), s>>>(a); break;
+    case 2 * kP2GThreads: k_p2g<2, kP2GStress><<<a.p2g_ctas, kP2GThreads, p2g_dyn_smem<2>(), s>>>(a); break;
+    case 4 * kP2GThreads: k_p2g<4, kP2GStress><<<a.p2g_ctas, kP2GThreads, p2g_dyn_smem<4>(), s>>>(a); break;
+    default: k_p2g<3, kP2GStress><<<a.p2g_ctas, kP2GThreads, p2g_dyn_smem<3>(), s>>>(a); break;
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_p2g_std(const StepArgs& a, cudaStream_t s)
+{
+    k_p2g_std<<<a.p2g_ctas, kStdThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_g2p_vc(const StepArgs& a, cudaStream_t s)
+{
+    k_g2p_vc<<<a.persistent_ctas, kVcThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+int occupancy_p2g_std()
+{
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_p2g_std, kStdThreads, 0);
+    return b;
 }
 
 cudaError_t launch_grid(const StepArgs& a, cudaStream_t s)
@@ -1283,29 +1496,41 @@ cudaError_t launch_grid(const StepArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <bool SOLIDS>
+template <int FLAGS>
 static void launch_g2p_variant(const StepArgs& a, cudaStream_t s)
 {
     const int c = a.persistent_ctas;
     if (a.g2p_regs64) {
         switch (a.g2p_threads) {
-        case 128: k_g2p<128, 8, SOLIDS><<<c, 128, 0, s>>>(a); break;
-        case 512: k_g2p<512, 2, SOLIDS><<<c, 512, 0, s>>>(a); break;
-        default: k_g2p<256, 4, SOLIDS><<<c, 256, 0, s>>>(a); break;
+        case 128: k_g2p<128, 8, FLAGS><<<c, 128, 0, s>>>(a); break;
+        case 512: k_g2p<512, 2, FLAGS><<<c, 512, 0, s>>>(a); break;
+        default: k_g2p<256, 4, FLAGS><<<c, 256, 0, s>>>(a); break;
         }
     } else {
         switch (a.g2p_threads) {
-        case 128: k_g2p<128, 6, SOLIDS><<<c, 128, 0, s>>>(a); break;
-        case 512: k_g2p<512, 1, SOLIDS><<<c, 512, 0, s>>>(a); break;
-        default: k_g2p<256, 3, SOLIDS><<<c, 256, 0, s>>>(a); break;
+        case 128: k_g2p<128, 6, FLAGS><<<c, 128, 0, s>>>(a); break;
+        case 512: k_g2p<512, 1, FLAGS><<<c, 512, 0, s>>>(a); break;
+        default: k_g2p<256, 3, FLAGS><<<c, 256, 0, s>>>(a); break;
         }
     }
 }
 
+// The standard-MPM and PB-MPM variants exist in the default launch shape only
+// (128 threads, 64 registers): the MLS-MPM shapes are what the tuner explores.
 cudaError_t launch_g2p(const StepArgs& a, cudaStream_t s)
 {
-    if (a.any_rigid) launch_g2p_variant<true>(a, s);
-    else launch_g2p_variant<false>(a, s);
+    const int c = a.persistent_ctas;
+    if (a.solver == MPM_SOLVER_STANDARD) {
+        if (a.any_rigid) k_g2p<128, 8, kG2PStdGrad | kG2PSolids><<<c, 128, 0, s>>>(a);
+        else k_g2p<128, 8, kG2PStdGrad><<<c, 128, 0, s>>>(a);
+    } else if (a.solver == MPM_SOLVER_PB) {
+        if (a.any_rigid) k_g2p<128, 8, kG2PNoStress | kG2PSolids><<<c, 128, 0, s>>>(a);
+        else k_g2p<128, 8, kG2PNoStress><<<c, 128, 0, s>>>(a);
+    } else if (a.any_rigid) {
+        launch_g2p_variant<kG2PSolids>(a, s);
+    } else {
+        launch_g2p_variant<0>(a, s);
+    }
     return cudaGetLastError();
 }
 
@@ -1363,11 +1588,11 @@ int occupancy_p2g(int chunk)
 {
     int b = 0;
     if (chunk == 2 * kP2GThreads)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_p2g<2>, kP2GThreads, p2g_dyn_smem<2>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_p2g<2, kP2GStress>, kP2GThreads, p2g_dyn_smem<2>());
     else if (chunk == 4 * kP2GThreads)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_p2g<4>, kP2GThreads, p2g_dyn_smem<4>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_p2g<4, kP2GStress>, kP2GThreads, p2g_dyn_smem<4>());
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_p2g<3>, kP2GThreads, p2g_dyn_smem<3>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_p2g<3, kP2GStress>, kP2GThreads, p2g_dyn_smem<3>());
     return b;
 }
 
@@ -1377,13 +1602,13 @@ int occupancy_g2p(int threads, int regs64)
     // shared memory; its occupancy bounds both
     int b = 0;
     if (regs64) {
-        if (threads == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<128, 8, true>, 128, 0);
-        else if (threads == 512) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<512, 2, true>, 512, 0);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<256, 4, true>, 256, 0);
+        if (threads == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<128, 8, kG2PSolids>, 128, 0);
+        else if (threads == 512) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<512, 2, kG2PSolids>, 512, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<256, 4, kG2PSolids>, 256, 0);
     } else {
-        if (threads == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<128, 6, true>, 128, 0);
-        else if (threads == 512) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<512, 1, true>, 512, 0);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<256, 3, true>, 256, 0);
+        if (threads == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<128, 6, kG2PSolids>, 128, 0);
+        else if (threads == 512) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<512, 1, kG2PSolids>, 512, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<256, 3, kG2PSolids>, 256, 0);
     }
     return b;
 }

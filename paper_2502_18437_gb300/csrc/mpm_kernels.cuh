@@ -60,6 +60,8 @@ struct StepArgs {
     int tau_valid;               // P2G reads the stored stress (else recomputes it from F)
     int any_rigid;               // some scene of the range has a rigid (contact in the grid update)
     int cell_order;              // P2G rewrites each pass's permutation slots in cell order
+    int solver;                  // MPM_SOLVER_*
+    float pb_beta;               // PB-MPM constraint blend
 };
 
 constexpr int kStateFloats = 32;  // x3 v3 C9 F9 tau6 mu lam (+ int id)
@@ -74,6 +76,9 @@ cudaError_t launch_p2g(const StepArgs& a, cudaStream_t s);
 cudaError_t prepare_p2g();  // shared-memory opt-in of the P2G variants (once per device, before any launch)
 cudaError_t launch_grid(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_g2p(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_p2g_std(const StepArgs& a, cudaStream_t s);  // standard MPM P2G
+cudaError_t launch_g2p_vc(const StepArgs& a, cudaStream_t s);   // PB-MPM cycle G2P (v, C in place)
+int occupancy_p2g_std();
 cudaError_t launch_g2p2g(const StepArgs& a, cudaStream_t s);
 int occupancy_g2p2g();
 int occupancy_grid();

@@ -24,6 +24,7 @@ STATUS = {
 }
 MEM_HOST, MEM_DEVICE = 0, 1
 MODELS = {"fixed_corotated": 0, "neo_hookean": 1}
+SOLVERS = {"mls": 0, "standard": 1, "pb": 2}
 RIGID_TYPES = {"sphere": 0, "box": 1, "quad_slicer": 2, "segments": 3, "none": -1}
 FIELD = {"x": 1, "v": 2, "C": 4, "F": 8, "order": 16, "impulse": 32}
 FIELD_SHAPE = {"x": (3,), "v": (3,), "C": (3, 3), "F": (3, 3), "order": ()}
@@ -46,7 +47,8 @@ class mpm_config(ct.Structure):
         ("max_particles", ct.c_int64), ("model", ct.c_int32), ("plasticity", ct.c_int32),
         ("yield_stress", ct.c_float), ("gravity", ct.c_float * 3), ("bound", ct.c_int32),
         ("floor_sticky", ct.c_int32), ("timeout_ms", ct.c_int32), ("tape_checkpoint_every", ct.c_int32),
-        ("tape_max_substeps", ct.c_int32), ("reserved", ct.c_int32 * 7),
+        ("tape_max_substeps", ct.c_int32), ("solver", ct.c_int32), ("pb_iterations", ct.c_int32),
+        ("pb_beta", ct.c_float), ("reserved", ct.c_int32 * 4),
     ]
 
 
@@ -279,7 +281,7 @@ class Simulation:
     def __init__(self, grid_n=64, max_particles=1 << 20, *, n_scenes=1, scene_grid_n=None,
                  model="fixed_corotated", plasticity=False, yield_stress=0.0, gravity=(0.0, -9.8, 0.0),
                  bound=3, floor_sticky=True, timeout_ms=20000, tape_checkpoint_every=0, tape_max_substeps=0,
-                 stream=None):
+                 solver="mls", pb_iterations=10, pb_beta=1.0, stream=None):
         cfg = mpm_config()
         cfg.n_scenes = int(n_scenes)
         cfg.grid_n = int(grid_n)
@@ -298,6 +300,9 @@ class Simulation:
         cfg.timeout_ms = int(timeout_ms)
         cfg.tape_checkpoint_every = int(tape_checkpoint_every)
         cfg.tape_max_substeps = int(tape_max_substeps)
+        cfg.solver = SOLVERS[solver] if isinstance(solver, str) else int(solver)
+        cfg.pb_iterations = int(pb_iterations)
+        cfg.pb_beta = float(pb_beta)
         self.n_scenes = n_scenes
         self.grid_n = list(scene_grid_n) if scene_grid_n is not None else [grid_n] * n_scenes
         self.stream = _default_stream() if stream is None else stream
