@@ -26,9 +26,11 @@ import numpy as np
 from . import build as _build
 
 MAX_PTS = 64
+MAX_TRIS = 64
+MAX_SPINE = 16
 ERR_OUT_OF_DOMAIN, ERR_NONFINITE, ERR_INVERTED = 1, 2, 4
 MODELS = {"fixed_corotated": 0, "neo_hookean": 1}
-RIGID_TYPES = {"sphere": 0, "box": 1, "quad_slicer": 2, "segments": 3}
+RIGID_TYPES = {"sphere": 0, "box": 1, "quad_slicer": 2, "segments": 3, "arc": 4, "mesh_slicer": 5}
 REGION = {0: "none", 1: "regular", 2: "oned", 3: "sticky"}
 
 
@@ -47,6 +49,8 @@ class Rigid(ct.Structure):
         ("c_d", ct.c_double), ("margin", ct.c_double), ("radius", ct.c_double),
         ("half", ct.c_double * 3), ("thickness", ct.c_double), ("spine_radius", ct.c_double),
         ("pts", ct.c_double * (MAX_PTS * 3)), ("impulse", ct.c_double * 6),
+        ("n_tris", ct.c_int), ("n_spine", ct.c_int), ("tris", ct.c_int * (MAX_TRIS * 3)),
+        ("spine", ct.c_int * MAX_SPINE),
     ]
 
 
@@ -161,6 +165,14 @@ def make_rigid(desc):
     r.n_pts = len(pts)
     for i, v in enumerate(pts.reshape(-1)):
         r.pts[i] = float(v)
+    tris = np.asarray(desc.get("tris", np.zeros((0, 3))), dtype=np.int64).reshape(-1, 3)
+    spine = np.asarray(desc.get("spine", []), dtype=np.int64).reshape(-1)
+    assert len(tris) <= MAX_TRIS and len(spine) <= MAX_SPINE
+    r.n_tris, r.n_spine = len(tris), len(spine)
+    for i, v in enumerate(tris.reshape(-1)):
+        r.tris[i] = int(v)
+    for i, v in enumerate(spine):
+        r.spine[i] = int(v)
     return r
 
 

@@ -28,10 +28,13 @@
 #include <string.h>
 
 #define ORC_MAX_PTS 64
+#define ORC_MAX_TRIS 64
+#define ORC_MAX_SPINE 16
+#define ORC_TWO_PI 6.283185307179586476925286766559
 
 enum { ORC_ERR_OUT_OF_DOMAIN = 1, ORC_ERR_NONFINITE = 2, ORC_ERR_INVERTED = 4 };
 enum { ORC_FIXED_COROTATED = 0, ORC_NEO_HOOKEAN = 1 };
-enum { ORC_SPHERE = 0, ORC_BOX = 1, ORC_QUAD_SLICER = 2, ORC_SEGMENTS = 3 };
+enum { ORC_SPHERE = 0, ORC_BOX = 1, ORC_QUAD_SLICER = 2, ORC_SEGMENTS = 3, ORC_ARC = 4, ORC_MESH_SLICER = 5 };
 enum { ORC_REGION_NONE = 0, ORC_REGION_REGULAR = 1, ORC_REGION_ONED = 2, ORC_REGION_STICKY = 3 };
 
 typedef struct {
@@ -59,8 +62,13 @@ typedef struct {
     double half[3];     /* box half extents; slicer: half[0] along the edge, half[1] spine->edge */
     double thickness;   /* slicer thickness */
     double spine_radius;/* slicer spine circle radius */
-    double pts[ORC_MAX_PTS * 3]; /* segment chain points, body frame */
+    double pts[ORC_MAX_PTS * 3]; /* segment chain points / mesh vertices, body frame */
     double impulse[6];  /* accumulated momentum given to the rigid: linear, angular about c */
+    /* arc: half[0] circle radius, half[1] start angle, half[2] sweep (radians, in
+       the body x-y plane, centred on the body origin); radius = wire radius */
+    int n_tris, n_spine;             /* mesh slicer: triangles, spine polyline points */
+    int tris[ORC_MAX_TRIS * 3];      /* vertex indices into pts */
+    int spine[ORC_MAX_SPINE];        /* vertex indices of the spine polyline */
 } orc_rigid;
 
 /* ---------------------------------------------------------------- helpers */
@@ -320,6 +328,80 @@ static void to_world(const orc_rigid* r, const double a[3], double out[3])
     for (int i = 0; i < 3; ++i) out[i] = r->R[3 * i] * a[0] + r->R[3 * i + 1] * a[1] + r->R[3 * i + 2] * a[2];
 }
 
+/* Nearest point q of segment [a, b] to p (endpoint projections keep the
+ * segment); returns |p - q|. */
+static double closest_on_segment(const double p[3], const double a[3], const double b[3], double q[3])
+{
+    double ab[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    double ap[3] = {p[0] - a[0], p[1] - a[1], p[2] - a[2]};
+    double L2 = dot3(ab, ab);
+    double u = L2 > 0 ? dot3(ap, ab) / L2 : 0.0;
+    if (u < 0) u = 0;
+    if (u > 1) u = 1;
+    for (int i = 0; i < 3; ++i) q[i] = a[i] + u * ab[i];
+    double d[3] = {p[0] - q[0], p[1] - q[1], p[2] - q[2]};
+    return sqrt(dot3(d, d));
+}
+
+/* Nearest point q of triangle (a, b, c) to p: the orthogonal projection when it
+ * falls inside (barycentric coordinates from the 2x2 normal equations of the
+ * plane's least-squares problem; *interior = 1), else the nearest of the three
+ * edges' nearest points (*interior = 0).  Returns |p - q|. */
+static double closest_on_triangle(const double p[3], const double a[3], const double b[3], const double c[3],
+                                  double q[3], int* interior)
+{
+    double e0[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, e1[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+    double ap[3] = {p[0] - a[0], p[1] - a[1], p[2] - a[2]};
+    double d00 = dot3(e0, e0), d01 = dot3(e0, e1), d11 = dot3(e1, e1), d20 = dot3(ap, e0), d21 = dot3(ap, e1);
+    double den = d00 * d11 - d01 * d01;
+    *interior = 0;
+    if (den > 0) {
+        double s = (d11 * d20 - d01 * d21) / den, t = (d00 * d21 - d01 * d20) / den;
+        if (s >= 0 && t >= 0 && s + t <= 1) {
+            for (int i = 0; i < 3; ++i) q[i] = a[i] + s * e0[i] + t * e1[i];
+            double d[3] = {p[0] - q[0], p[1] - q[1], p[2] - q[2]};
+            *interior = 1;
+            return sqrt(dot3(d, d));
+        }
+    }
+    double qa[3], qb[3], qc[3];
+    double da = closest_on_segment(p, a, b, qa), db = closest_on_segment(p, b, c, qb), dc = closest_on_segment(p, c, a, qc);
+    double best = da;
+    memcpy(q, qa, sizeof qa);
+    if (db < best) { best = db; memcpy(q, qb, sizeof qb); }
+    if (dc < best) { best = dc; memcpy(q, qc, sizeof qc); }
+    return best;
+}
+
+/* Nearest point of the arc (circle of radius Ra about the body origin in the
+ * body x-y plane, angles th0 .. th0 + sweep) to the body point p, and the unit
+ * tangent there (direction of increasing angle).  A point on the circle's
+ * axis has every angle at the same distance and takes the start angle. */
+static double closest_on_arc(const double p[3], double Ra, double th0, double sweep, double q[3], double t[3])
+{
+    double th;
+    if (p[0] == 0.0 && p[1] == 0.0) {
+        th = th0;
+    } else {
+        double phi = atan2(p[1], p[0]);
+        double rel = fmod(phi - th0, ORC_TWO_PI);
+        if (rel < 0) rel += ORC_TWO_PI;
+        if (rel <= sweep) {
+            th = th0 + rel;
+        } else {
+            /* outside the sweep: the nearer endpoint */
+            double qe0[3] = {Ra * cos(th0), Ra * sin(th0), 0.0};
+            double qe1[3] = {Ra * cos(th0 + sweep), Ra * sin(th0 + sweep), 0.0};
+            double d0[3] = {p[0] - qe0[0], p[1] - qe0[1], p[2]}, d1[3] = {p[0] - qe1[0], p[1] - qe1[1], p[2]};
+            th = dot3(d1, d1) < dot3(d0, d0) ? th0 + sweep : th0;
+        }
+    }
+    q[0] = Ra * cos(th); q[1] = Ra * sin(th); q[2] = 0.0;
+    t[0] = -sin(th); t[1] = cos(th); t[2] = 0.0;
+    double d[3] = {p[0] - q[0], p[1] - q[1], p[2] - q[2]};
+    return sqrt(dot3(d, d));
+}
+
 /* Region test and contact frame of one rigid at world point xw.
  * Returns the region code; n (unit normal, world) and t (unit tangent, world,
  * ONED only) are filled when the code is not NONE; *dist receives the distance
@@ -337,7 +419,15 @@ static void to_world(const orc_rigid* r, const double a[3], double out[3])
  *  - connected segments (Sec. IV-C): 1D geometry; nearest segment wins (ties
  *    to the lower index); node in contact when the distance is below
  *    radius + margin; n from the projected point to the node, t along the
- *    segment.  A node on the centre line has no normal: n is left zero. */
+ *    segment.  A node on the centre line has no normal: n is left zero.
+ *  - arc (Sec. IV-C, the suture needle): 1D geometry like the segments, with
+ *    the arc's tangent at the nearest point as t;
+ *  - triangle-mesh slicer (Sec. IV-B): a blade given as an open triangle mesh
+ *    of thickness h and a spine polyline.  A node closer than spine_radius +
+ *    margin to the spine gets sticky contact; otherwise a node closer than
+ *    h/2 + margin to the nearest triangle (lowest index on ties) gets regular
+ *    contact with normal sign((x - q) . n_T) n_T where its nearest point q lies
+ *    inside the triangle (0 counts as +), and (x - q)/|x - q| off it. */
 int orc_geometry(const orc_rigid* r, const double xw[3], double n[3], double t[3], double* dist)
 {
     double d[3] = {xw[0] - r->c[0], xw[1] - r->c[1], xw[2] - r->c[2]}, p[3];
@@ -386,6 +476,55 @@ int orc_geometry(const orc_rigid* r, const double xw[3], double n[3], double t[3
                 code = ORC_REGION_REGULAR;
                 if (fabs(p[0]) <= a && fabs(p[1]) <= b) nl[2] = p[2] >= 0 ? 1.0 : -1.0;
                 else { nl[0] = dv[0] / l; nl[1] = dv[1] / l; nl[2] = dv[2] / l; }
+            }
+        }
+    } else if (r->type == ORC_ARC) {
+        double q[3], tt[3];
+        double l = closest_on_arc(p, r->half[0], r->half[1], r->half[2], q, tt);
+        *dist = l;
+        if (l < r->radius + r->margin) {
+            code = ORC_REGION_ONED;
+            if (l > 0) for (int i = 0; i < 3; ++i) nl[i] = (p[i] - q[i]) / l;
+            memcpy(tl, tt, sizeof tl);
+        }
+    } else if (r->type == ORC_MESH_SLICER) {
+        double dsp = INFINITY;
+        for (int k = 0; k + 1 < r->n_spine; ++k) {
+            double q[3];
+            double l = closest_on_segment(p, r->pts + 3 * r->spine[k], r->pts + 3 * r->spine[k + 1], q);
+            if (l < dsp) dsp = l;
+        }
+        if (dsp < r->spine_radius + r->margin) {
+            *dist = dsp;
+            code = ORC_REGION_STICKY;
+        } else {
+            double best = INFINITY, bq[3] = {0, 0, 0};
+            int bt = -1, binside = 0;
+            for (int k = 0; k < r->n_tris; ++k) {
+                double q[3];
+                int inside;
+                const int* tv = r->tris + 3 * k;
+                double l = closest_on_triangle(p, r->pts + 3 * tv[0], r->pts + 3 * tv[1], r->pts + 3 * tv[2], q, &inside);
+                if (l < best) { best = l; memcpy(bq, q, sizeof bq); bt = k; binside = inside; }
+            }
+            *dist = best;
+            if (bt >= 0 && best < 0.5 * r->thickness + r->margin) {
+                code = ORC_REGION_REGULAR;
+                if (binside) {
+                    const int* tv = r->tris + 3 * bt;
+                    const double* a = r->pts + 3 * tv[0];
+                    const double* b = r->pts + 3 * tv[1];
+                    const double* c = r->pts + 3 * tv[2];
+                    double e0[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, e1[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+                    double nt[3];
+                    cross3(e0, e1, nt);
+                    double ln = sqrt(dot3(nt, nt));
+                    double dp[3] = {p[0] - bq[0], p[1] - bq[1], p[2] - bq[2]};
+                    double sg = dot3(dp, nt) >= 0 ? 1.0 : -1.0;
+                    for (int i = 0; i < 3; ++i) nl[i] = sg * nt[i] / ln;
+                } else if (best > 0) {
+                    for (int i = 0; i < 3; ++i) nl[i] = (p[i] - bq[i]) / best;
+                }
             }
         }
     } else if (r->type == ORC_SEGMENTS) {

@@ -67,6 +67,51 @@ def segments(center, quat, pts, *, radius, vel=(0, 0, 0), omega=(0, 0, 0), mu_k=
                 radius=radius, vel=tuple(vel), omega=tuple(omega), mu_k=mu_k, c_d=c_d, margin=margin)
 
 
+def arc(center, quat, *, arc_radius, start, sweep, radius, vel=(0, 0, 0), omega=(0, 0, 0), mu_k=0.3, c_d=1.0,
+        margin=0.0):
+    """Curved suture needle (Sec. IV-C): the circle of radius arc_radius about
+    the body origin in the body x-y plane, from angle ``start`` over ``sweep``
+    radians, with wire radius ``radius``."""
+    return dict(type="arc", center=tuple(center), quat=tuple(quat), half=(arc_radius, start, sweep), radius=radius,
+                vel=tuple(vel), omega=tuple(omega), mu_k=mu_k, c_d=c_d, margin=margin)
+
+
+def mesh_slicer(center, quat, pts, tris, spine, *, thickness, spine_radius=None, vel=(0, 0, 0), omega=(0, 0, 0),
+                mu_k=0.3, c_d=1.0, margin=0.0):
+    """Blade given as an open triangle mesh (Sec. IV-B, TriangleMeshSlicer):
+    vertices ``pts`` (body frame), triangles ``tris`` (vertex indices), the
+    spine as a polyline of vertex indices ``spine``, blade thickness."""
+    return dict(type="mesh_slicer", center=tuple(center), quat=tuple(quat), pts=np.asarray(pts, float),
+                tris=np.asarray(tris, int), spine=np.asarray(spine, int), thickness=thickness,
+                spine_radius=0.5 * thickness if spine_radius is None else spine_radius, vel=tuple(vel),
+                omega=tuple(omega), mu_k=mu_k, c_d=c_d, margin=margin)
+
+
+def curved_blade_mesh(half_edge=0.08, depth=0.06, bend=0.02, nu=8, nv=4, seed=6, jitter=0.1):
+    """A seeded curved scalpel blade: a (nu+1) x (nv+1) vertex grid over body
+    x in [-half_edge, half_edge] (along the edge) and body y in [-depth/2, depth/2]
+    (spine at -depth/2, cutting edge at +depth/2), bent out of the x-y plane by
+    z = bend (x / half_edge)^2 and jittered inside the grid; two triangles per
+    cell.  Returns (pts, tris, spine)."""
+    g = rng(seed)
+    xs = np.linspace(-half_edge, half_edge, nu + 1)
+    ys = np.linspace(-depth / 2, depth / 2, nv + 1)
+    X, Y = np.meshgrid(xs, ys, indexing="ij")
+    dxg, dyg = xs[1] - xs[0], ys[1] - ys[0]
+    X = X + jitter * dxg * g.uniform(-1, 1, X.shape) * (np.abs(X) < half_edge - 1e-12)
+    Y = Y + jitter * dyg * g.uniform(-1, 1, Y.shape) * (np.abs(Y) < depth / 2 - 1e-12)
+    Z = bend * (X / half_edge) ** 2
+    pts = np.stack([X, Y, Z], -1).reshape(-1, 3)
+    idx = lambda i, j: i * (nv + 1) + j
+    tris = []
+    for i in range(nu):
+        for j in range(nv):
+            tris.append((idx(i, j), idx(i + 1, j), idx(i + 1, j + 1)))
+            tris.append((idx(i, j), idx(i + 1, j + 1), idx(i, j + 1)))
+    spine = [idx(i, 0) for i in range(nu + 1)]
+    return pts, np.array(tris), np.array(spine)
+
+
 def sphere(center, radius, *, vel=(0, 0, 0), omega=(0, 0, 0), mu_k=0.3, c_d=1.0, margin=0.0,
            quat=(1, 0, 0, 0)):
     return dict(type="sphere", center=tuple(center), quat=tuple(quat), radius=radius, vel=tuple(vel),

@@ -842,3 +842,90 @@ def test_pb_gravity_enters_once_per_step():
         assert np.max(np.abs(st.v - (v0 + dt * gvec))) < 1e-12
         assert np.max(np.abs(st.x - (x0 + dt * (v0 + dt * gvec)))) < 1e-13
         assert np.max(np.abs(st.F - np.eye(3))) < 1e-12
+
+
+# ------------------------------------------------- arc and mesh slicer
+
+def test_arc_sdf_brute_force_and_tangent():
+    # Sec. IV-C arc (suture needle): distance to the nearest point of the arc
+    # against dense sampling of the arc; the tangent is the unit vector along
+    # increasing angle at that point, perpendicular to its radius.
+    q = np.array([0.9, 0.3, -0.2, 0.25])
+    r = oracle.make_rigid(W.arc((0.5, 0.45, 0.55), tuple(q / np.linalg.norm(q)), arc_radius=0.06, start=0.4,
+                                sweep=3.5, radius=0.003, margin=1.0))
+    c, Rm = oracle.rigid_pose(r)
+    th = 0.4 + np.linspace(0.0, 3.5, 200001)
+    samples = c + (0.06 * np.stack([np.cos(th), np.sin(th), 0 * th], -1)) @ Rm.T
+    g = np.random.default_rng(35)
+    for _ in range(100):
+        x = c + g.uniform(-0.12, 0.12, 3)
+        code, n, t, d = oracle.geometry(r, x)
+        ref = np.min(np.linalg.norm(samples - x, axis=1))
+        assert abs(d - ref) < 1e-8, (d, ref)
+        assert code == "oned"
+        qpt = x - d * n  # the nearest point
+        rad = Rm.T @ (qpt - c)
+        assert abs(np.linalg.norm(rad[:2]) - 0.06) < 1e-12 and abs(rad[2]) < 1e-12
+        assert abs(np.linalg.norm(t) - 1) < 1e-12 and abs(np.dot(t, qpt - c)) < 1e-12
+
+
+def _flat_mesh(a, b):
+    pts = [(-a, -b, 0.0), (a, -b, 0.0), (a, b, 0.0), (-a, b, 0.0)]
+    return pts, [(0, 1, 2), (0, 2, 3)], [0, 1]
+
+
+def test_flat_mesh_slicer_equals_quad_slicer():
+    # A triangle-mesh slicer (Sec. IV-B) made of the quad's two triangles with
+    # the spine along the quad's y = -b edge is the QuadSlicer (pinned against
+    # brute-force sampling): same regions, distances and normals everywhere.
+    a, b, h = 0.07, 0.04, 0.006
+    q = np.array([0.8, -0.3, 0.4, 0.2])
+    q = tuple(q / np.linalg.norm(q))
+    kw = dict(thickness=h, spine_radius=0.004, margin=0.002)
+    quad = oracle.make_rigid(W.quad_slicer((0.5, 0.5, 0.5), q, half_edge=a, half_depth=b, **kw))
+    pts, tris, spine = _flat_mesh(a, b)
+    mesh = oracle.make_rigid(W.mesh_slicer((0.5, 0.5, 0.5), q, pts, tris, spine, **kw))
+    g = np.random.default_rng(36)
+    seen = set()
+    for _ in range(3000):
+        x = 0.5 + g.uniform(-0.1, 0.1, 3) * np.array([1.0, 1.0, 0.15]) @ np.eye(3)
+        cq, nq, _, dq = oracle.geometry(quad, x)
+        cm, nm, _, dm = oracle.geometry(mesh, x)
+        assert cq == cm
+        seen.add(cq)
+        assert abs(dq - dm) < 1e-13
+        assert np.max(np.abs(nq - nm)) < 1e-12
+    assert {"none", "regular", "sticky"} <= seen
+
+
+def test_curved_mesh_slicer_brute_force():
+    # Curved, jittered blade mesh: the distance used by the region test is the
+    # distance to the nearest surface point (no sampled surface point is closer,
+    # and the sampled minimum is within the sampling error), and the normal is
+    # a unit vector from that point toward the query (face interiors: the
+    # face normal, signed by side).
+    pts, tris, spine = W.curved_blade_mesh()
+    # no spine here (the wide margin would make every point sticky)
+    r = oracle.make_rigid(W.mesh_slicer((0.5, 0.5, 0.5), (1, 0, 0, 0), pts, tris, [], thickness=0.004,
+                                        spine_radius=0.002, margin=1.0))
+    u = np.linspace(0, 1, 41)
+    U, V = np.meshgrid(u, u, indexing="ij")
+    keep = U + V <= 1
+    U, V = U[keep], V[keep]
+    samples = np.concatenate([pts[t0] + U[:, None] * (pts[t1] - pts[t0]) + V[:, None] * (pts[t2] - pts[t0])
+                              for t0, t1, t2 in tris]) + 0.5
+    g = np.random.default_rng(37)
+    n_regular = 0
+    for _ in range(150):
+        x = 0.5 + g.uniform(-1, 1, 3) * np.array([0.1, 0.05, 0.04])
+        code, n, _, d = oracle.geometry(r, x)
+        if code != "regular":
+            continue
+        n_regular += 1
+        dist = np.linalg.norm(samples - x, axis=1)
+        assert d <= dist.min() + 1e-12
+        assert dist.min() - d < 2e-5  # sampling error of a 40 x 40 barycentric grid
+        assert abs(np.linalg.norm(n) - 1) < 1e-12
+        qpt = x - d * n  # lies on the mesh, at distance d
+        assert np.linalg.norm(samples - qpt, axis=1).min() < 3e-3
+    assert n_regular > 100
