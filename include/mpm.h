@@ -73,9 +73,12 @@ enum { MPM_PLASTIC_NONE = 0, MPM_PLASTIC_VON_MISES = 1 };
  * substep, contact and walls act in every cycle (their momentum is booked to
  * the rigids in every cycle), plasticity and mpm_backward are not available. */
 enum { MPM_SOLVER_MLS = 0, MPM_SOLVER_STANDARD = 1, MPM_SOLVER_PB = 2 };
-enum { MPM_SPHERE = 0, MPM_BOX = 1, MPM_QUAD_SLICER = 2, MPM_SEGMENTS = 3, MPM_RIGID_NONE = -1 };
+enum { MPM_SPHERE = 0, MPM_BOX = 1, MPM_QUAD_SLICER = 2, MPM_SEGMENTS = 3, MPM_ARC = 4, MPM_MESH_SLICER = 5,
+       MPM_RIGID_NONE = -1 };
 
 #define MPM_MAX_SEGMENT_POINTS 64
+#define MPM_MAX_MESH_TRIANGLES 64
+#define MPM_MAX_SPINE_POINTS 16
 #define MPM_MAX_RIGIDS 8 /* per scene */
 
 /* fields of mpm_read_state / mpm_write_state (bitmask; buffers in bit order) */
@@ -148,7 +151,21 @@ typedef struct {
  *                  around the segment y = -half[1] (Sec. IV-B)
  *  MPM_SEGMENTS    chain of n_points >= 2 points (body frame) with radius;
  *                  1D contact keeping only the tangential slip (Sec. IV-C)
- * mu_k is the kinetic friction coefficient and c_d the drag factor of Eq. 11. */
+ *  MPM_ARC         curved needle (Sec. IV-C): the circle of radius half[0]
+ *                  about the body origin in the body x-y plane, from angle
+ *                  half[1] over half[2] (0 < half[2] <= 2 pi) radians, wire
+ *                  radius `radius`; 1D contact along the arc tangent
+ *  MPM_MESH_SLICER blade given as an open triangle mesh (Sec. IV-B,
+ *                  TriangleMeshSlicer): n_points vertices in points (body
+ *                  frame), n_triangles triangles (vertex indices), thickness;
+ *                  sticky spine circle of spine_radius around the polyline
+ *                  through the n_spine vertices listed in spine (0 or >= 2).
+ *                  Normal: the face normal signed by side where the nearest
+ *                  point lies inside a triangle, else the nearest-point
+ *                  direction.
+ * mu_k is the kinetic friction coefficient and c_d the drag factor of Eq. 11.
+ * Particles that end a substep inside a sphere or a box are pushed out to its
+ * surface (Sec. IV-A); blades, needles and segments push nothing out. */
 typedef struct {
     int32_t type;
     int32_t n_points;
@@ -162,6 +179,10 @@ typedef struct {
     float thickness;
     float spine_radius;
     float points[MPM_MAX_SEGMENT_POINTS][3];
+    int32_t n_triangles;                           /* MPM_MESH_SLICER */
+    int32_t n_spine;                               /* MPM_MESH_SLICER */
+    int32_t triangles[MPM_MAX_MESH_TRIANGLES][3];  /* vertex indices into points */
+    int32_t spine[MPM_MAX_SPINE_POINTS];           /* vertex indices into points */
 } mpm_rigid;
 
 typedef struct mpm_ctx mpm_ctx; /* opaque; owned by the library */

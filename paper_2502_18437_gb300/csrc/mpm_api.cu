@@ -178,8 +178,14 @@ StepArgs step_args(mpm_ctx* c, float dt, int s0, int s1, const PState& in, const
         a.p2g_ctas = c->num_sms * c->occ_p2g_std;
     }
     a.any_rigid = 0;
-    for (int sc = s0; sc < s1; ++sc)
+    a.rigid_ext = 0;
+    for (int sc = s0; sc < s1; ++sc) {
         if (c->h_scenes[sc].n_rigid > 0) a.any_rigid = 1;
+        for (int k = 0; k < kMaxRigids; ++k) {
+            const int ty = c->rigid_type[(size_t)sc * kMaxRigids + k];
+            if (ty == MPM_ARC || ty == MPM_MESH_SLICER) a.rigid_ext = 1;
+        }
+    }
     return a;
 }
 
@@ -631,13 +637,33 @@ extern "C" int mpm_set_rigid(mpm_ctx* c, int scene, int rigid_id, const mpm_rigi
     if (r->type == MPM_RIGID_NONE) {
         d.type = MPM_RIGID_NONE;
     } else {
-        if (r->type < MPM_SPHERE || r->type > MPM_SEGMENTS) return MPM_ERR_INVALID_ARGUMENT;
+        if (r->type < MPM_SPHERE || r->type > MPM_MESH_SLICER) return MPM_ERR_INVALID_ARGUMENT;
         if (r->type == MPM_SEGMENTS && (r->n_points < 2 || r->n_points > MPM_MAX_SEGMENT_POINTS)) return MPM_ERR_INVALID_ARGUMENT;
+        if (r->type == MPM_ARC && !(r->half[0] > 0.f && r->half[2] > 0.f && r->half[2] <= 6.2831855f))
+            return MPM_ERR_INVALID_ARGUMENT;
+        if (r->type == MPM_MESH_SLICER) {
+            if (r->n_points < 3 || r->n_points > MPM_MAX_SEGMENT_POINTS || r->n_triangles < 1 ||
+                r->n_triangles > MPM_MAX_MESH_TRIANGLES || r->n_spine < 0 || r->n_spine == 1 ||
+                r->n_spine > MPM_MAX_SPINE_POINTS)
+                return MPM_ERR_INVALID_ARGUMENT;
+            for (int k = 0; k < 3 * r->n_triangles; ++k) {
+                const int v = (&r->triangles[0][0])[k];
+                if (v < 0 || v >= r->n_points) return MPM_ERR_INVALID_ARGUMENT;
+            }
+            for (int k = 0; k < r->n_spine; ++k)
+                if (r->spine[k] < 0 || r->spine[k] >= r->n_points) return MPM_ERR_INVALID_ARGUMENT;
+        }
         const double qn = std::sqrt((double)r->quat[0] * r->quat[0] + (double)r->quat[1] * r->quat[1] +
                                     (double)r->quat[2] * r->quat[2] + (double)r->quat[3] * r->quat[3]);
         if (!(qn > 0.0)) return MPM_ERR_INVALID_ARGUMENT;
         d.type = r->type;
-        d.n_pts = r->type == MPM_SEGMENTS ? r->n_points : 0;
+        d.n_pts = (r->type == MPM_SEGMENTS || r->type == MPM_MESH_SLICER) ? r->n_points : 0;
+        if (r->type == MPM_MESH_SLICER) {
+            d.n_tris = r->n_triangles;
+            d.n_spine = r->n_spine;
+            for (int k = 0; k < 3 * d.n_tris; ++k) d.shape.tris[k] = (unsigned char)(&r->triangles[0][0])[k];
+            for (int k = 0; k < d.n_spine; ++k) d.shape.spine[k] = (unsigned char)r->spine[k];
+        }
         for (int i = 0; i < 3; ++i) {
             d.c0[i] = r->center[i];
             d.vel[i] = r->vel[i];
@@ -652,9 +678,10 @@ extern "C" int mpm_set_rigid(mpm_ctx* c, int scene, int rigid_id, const mpm_rigi
         d.thickness = r->thickness;
         d.spine_radius = r->spine_radius;
         d.t_set = c->h_time;
-        for (int k = 0; k < 3 * d.n_pts; ++k) d.pts[k] = (&r->points[0][0])[k];
+        for (int k = 0; k < 3 * d.n_pts; ++k) d.shape.pts[k] = (&r->points[0][0])[k];
     }
     c->h_rigids[slot] = d;
+    if (c->rigid_type[slot] != d.type) clear_graphs(c);  // captured launches carry the kinds of rigids
     c->rigid_type[slot] = d.type;
     int nr = 0;
     for (int k = 0; k < kMaxRigids; ++k)

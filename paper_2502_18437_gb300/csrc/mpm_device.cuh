@@ -39,24 +39,35 @@ struct SceneDev {
     float mu, lam;   // uniform Lame parameters (pp_mat == 0)
 };
 
+constexpr int kMaxTris = MPM_MAX_MESH_TRIANGLES;
+constexpr int kMaxSpine = MPM_MAX_SPINE_POINTS;
+
+// Shape data shared by the device copy and the staged pose: segment points or
+// mesh vertices (body frame) and the mesh's triangles and spine polyline.
+struct RigidShape {
+    float pts[kMaxPts * 3];
+    unsigned char tris[kMaxTris * 3];  // vertex indices (< kMaxPts)
+    unsigned char spine[kMaxSpine];
+};
+
 struct RigidDev {
-    int type, n_pts;
+    int type, n_pts, n_tris, n_spine;
     float c0[3], q0[4], vel[3], omega[3];
     float mu_k, c_d, margin, radius;
     float half[3];
     float thickness, spine_radius;
     double t_set;    // scene time at which (c0, q0) was the pose
-    float pts[kMaxPts * 3];
+    RigidShape shape;
 };
 
 // Pose of a rigid at the current scene time, staged in shared memory.
 struct RigidCur {
-    int type, n_pts;
+    int type, n_pts, n_tris, n_spine;
     float c[3], R[9], vel[3], omega[3];
     float mu_k, c_d, margin, radius;
     float half[3];
     float thickness, spine_radius;
-    float pts[kMaxPts * 3];
+    RigidShape shape;
 };
 
 // Pose of a solid rigid (sphere, box) at the end of the substep, for the

@@ -488,9 +488,106 @@ __global__ void __launch_bounds__(kP2GThreads, 4) k_p2g(StepArgs a)
 
 // ----------------------------------------------------------- grid update
 
+
+// Nearest point q of segment [a, b] to p (endpoint projections keep the
+// segment); returns |p - q|.
+__device__ __forceinline__ float closest_on_segment_f(float p0, float p1, float p2, const float* a, const float* b,
+                                                      float q[3])
+{
+    const float e0 = b[0] - a[0], e1 = b[1] - a[1], e2 = b[2] - a[2];
+    const float L2 = e0 * e0 + e1 * e1 + e2 * e2;
+    float u = L2 > 0.f ? ((p0 - a[0]) * e0 + (p1 - a[1]) * e1 + (p2 - a[2]) * e2) / L2 : 0.f;
+    u = fminf(fmaxf(u, 0.f), 1.f);
+    q[0] = a[0] + u * e0;
+    q[1] = a[1] + u * e1;
+    q[2] = a[2] + u * e2;
+    const float d0 = p0 - q[0], d1 = p1 - q[1], d2 = p2 - q[2];
+    return sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+}
+
+// Nearest point q of triangle (a, b, c) to p: the orthogonal projection when
+// its barycentric coordinates (2x2 normal equations of the plane) lie inside
+// (inside = true), else the nearest of the three edges' nearest points.
+__device__ __forceinline__ float closest_on_triangle_f(float p0, float p1, float p2, const float* a, const float* b,
+                                                       const float* c, float q[3], bool& inside)
+{
+    const float e0[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, e1[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+    const float ap[3] = {p0 - a[0], p1 - a[1], p2 - a[2]};
+    const float d00 = e0[0] * e0[0] + e0[1] * e0[1] + e0[2] * e0[2];
+    const float d01 = e0[0] * e1[0] + e0[1] * e1[1] + e0[2] * e1[2];
+    const float d11 = e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2];
+    const float d20 = ap[0] * e0[0] + ap[1] * e0[1] + ap[2] * e0[2];
+    const float d21 = ap[0] * e1[0] + ap[1] * e1[1] + ap[2] * e1[2];
+    const float den = d00 * d11 - d01 * d01;
+    inside = false;
+    if (den > 0.f) {
+        const float s = (d11 * d20 - d01 * d21) / den, t = (d00 * d21 - d01 * d20) / den;
+        if (s >= 0.f && t >= 0.f && s + t <= 1.f) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) q[i] = a[i] + s * e0[i] + t * e1[i];
+            inside = true;
+            const float d0 = p0 - q[0], d1 = p1 - q[1], d2 = p2 - q[2];
+            return sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+        }
+    }
+    float qa[3], qb[3], qc[3];
+    const float da = closest_on_segment_f(p0, p1, p2, a, b, qa), db = closest_on_segment_f(p0, p1, p2, b, c, qb),
+                dc = closest_on_segment_f(p0, p1, p2, c, a, qc);
+    float best = da;
+    q[0] = qa[0]; q[1] = qa[1]; q[2] = qa[2];
+    if (db < best) { best = db; q[0] = qb[0]; q[1] = qb[1]; q[2] = qb[2]; }
+    if (dc < best) { best = dc; q[0] = qc[0]; q[1] = qc[1]; q[2] = qc[2]; }
+    return best;
+}
+
+// Region of the triangle-mesh slicer at body point p (3 sticky spine, 1
+// regular, 0 none) and its body-frame normal nl.
+__device__ __forceinline__ int mesh_slicer_region(const RigidCur& R, float p0, float p1, float p2, float nl[3])
+{
+    float dsp = 3.4e38f;
+    for (int k = 0; k + 1 < R.n_spine; ++k) {
+        const float* a = R.shape.pts + 3 * R.shape.spine[k];
+        const float* b = R.shape.pts + 3 * R.shape.spine[k + 1];
+        float q[3];
+        dsp = fminf(dsp, closest_on_segment_f(p0, p1, p2, a, b, q));
+    }
+    if (dsp < R.spine_radius + R.margin) return 3;
+    float best = 3.4e38f, bq[3] = {0.f, 0.f, 0.f};
+    int bt = -1;
+    bool binside = false;
+    for (int k = 0; k < R.n_tris; ++k) {
+        const unsigned char* tv = R.shape.tris + 3 * k;
+        float q[3];
+        bool inside;
+        const float l = closest_on_triangle_f(p0, p1, p2, R.shape.pts + 3 * tv[0], R.shape.pts + 3 * tv[1],
+                                              R.shape.pts + 3 * tv[2], q, inside);
+        if (l < best) { best = l; bq[0] = q[0]; bq[1] = q[1]; bq[2] = q[2]; bt = k; binside = inside; }
+    }
+    if (bt < 0 || !(best < 0.5f * R.thickness + R.margin)) return 0;
+    if (binside) {
+        const unsigned char* tv = R.shape.tris + 3 * bt;
+        const float* a = R.shape.pts + 3 * tv[0];
+        const float* b = R.shape.pts + 3 * tv[1];
+        const float* c = R.shape.pts + 3 * tv[2];
+        const float e0[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+        const float e1[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+        const float m0 = e0[1] * e1[2] - e0[2] * e1[1], m1 = e0[2] * e1[0] - e0[0] * e1[2],
+                    m2 = e0[0] * e1[1] - e0[1] * e1[0];
+        const float ln = sqrtf(m0 * m0 + m1 * m1 + m2 * m2);
+        const float sg = ((p0 - bq[0]) * m0 + (p1 - bq[1]) * m1 + (p2 - bq[2]) * m2) >= 0.f ? 1.f : -1.f;
+        nl[0] = sg * m0 / ln; nl[1] = sg * m1 / ln; nl[2] = sg * m2 / ln;
+    } else if (best > 0.f) {
+        nl[0] = (p0 - bq[0]) / best; nl[1] = (p1 - bq[1]) / best; nl[2] = (p2 - bq[2]) / best;
+    }
+    return 1;
+}
+
 // Region test of one rigid at world point x (Sec. IV).  Returns 0 none,
 // 1 regular, 2 one-dimensional (segments), 3 sticky (slicer spine); n is the
 // contact normal (zero when undefined) and t the 1D tangent.
+// EXT: the launch has arcs or mesh slicers (a separate instance of the grid
+// kernel, so that the common shapes keep their registers).
+template <bool EXT>
 __device__ int rigid_region(const RigidCur& R, float3 x, float3& n, float3& t)
 {
     const float dx0 = x.x - R.c[0], dx1 = x.y - R.c[1], dx2 = x.z - R.c[2];
@@ -540,12 +637,44 @@ __device__ int rigid_region(const RigidCur& R, float3 x, float3& n, float3& t)
                 else { nl0 = d0 / l; nl1 = d1 / l; nl2 = d2 / l; }
             }
         }
+    } else if (EXT && R.type == MPM_ARC) {
+        // nearest point of the arc (radius half[0], angles half[1] .. half[1] + half[2])
+        const float Ra = R.half[0], th0 = R.half[1], sw = R.half[2];
+        const float kTwoPi = 6.28318530717958647f;
+        float th = th0;
+        if (p0 != 0.f || p1 != 0.f) {
+            float rel = fmodf(atan2f(p1, p0) - th0, kTwoPi);
+            if (rel < 0.f) rel += kTwoPi;
+            if (rel <= sw) {
+                th = th0 + rel;
+            } else {
+                float s0, c0, s1, c1;
+                sincosf(th0, &s0, &c0);
+                sincosf(th0 + sw, &s1, &c1);
+                const float a0 = p0 - Ra * c0, a1 = p1 - Ra * s0, b0 = p0 - Ra * c1, b1 = p1 - Ra * s1;
+                th = (b0 * b0 + b1 * b1 < a0 * a0 + a1 * a1) ? th0 + sw : th0;
+            }
+        }
+        float sn, cs;
+        sincosf(th, &sn, &cs);
+        const float d0 = p0 - Ra * cs, d1 = p1 - Ra * sn, d2 = p2;
+        const float l = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+        if (l < R.radius + R.margin) {
+            code = 2;
+            if (l > 0.f) { nl0 = d0 / l; nl1 = d1 / l; nl2 = d2 / l; }
+            tl0 = -sn;
+            tl1 = cs;
+        }
+    } else if (EXT && R.type == MPM_MESH_SLICER) {
+        float nl[3] = {0.f, 0.f, 0.f};
+        code = mesh_slicer_region(R, p0, p1, p2, nl);
+        nl0 = nl[0]; nl1 = nl[1]; nl2 = nl[2];
     } else if (R.type == MPM_SEGMENTS) {
         float best = 3.4e38f, bq0 = 0.f, bq1 = 0.f, bq2 = 0.f;
         int bs = -1;
         for (int s = 0; s + 1 < R.n_pts; ++s) {
-            const float a0 = R.pts[3 * s], a1 = R.pts[3 * s + 1], a2 = R.pts[3 * s + 2];
-            const float e0 = R.pts[3 * s + 3] - a0, e1 = R.pts[3 * s + 4] - a1, e2 = R.pts[3 * s + 5] - a2;
+            const float a0 = R.shape.pts[3 * s], a1 = R.shape.pts[3 * s + 1], a2 = R.shape.pts[3 * s + 2];
+            const float e0 = R.shape.pts[3 * s + 3] - a0, e1 = R.shape.pts[3 * s + 4] - a1, e2 = R.shape.pts[3 * s + 5] - a2;
             const float L2 = e0 * e0 + e1 * e1 + e2 * e2;
             float u = L2 > 0.f ? ((p0 - a0) * e0 + (p1 - a1) * e1 + (p2 - a2) * e2) / L2 : 0.f;
             u = fminf(fmaxf(u, 0.f), 1.f);
@@ -557,8 +686,8 @@ __device__ int rigid_region(const RigidCur& R, float3 x, float3& n, float3& t)
         if (bs >= 0 && best < R.radius + R.margin) {
             code = 2;
             if (best > 0.f) { nl0 = (p0 - bq0) / best; nl1 = (p1 - bq1) / best; nl2 = (p2 - bq2) / best; }
-            const float e0 = R.pts[3 * bs + 3] - R.pts[3 * bs], e1 = R.pts[3 * bs + 4] - R.pts[3 * bs + 1],
-                        e2 = R.pts[3 * bs + 5] - R.pts[3 * bs + 2];
+            const float e0 = R.shape.pts[3 * bs + 3] - R.shape.pts[3 * bs], e1 = R.shape.pts[3 * bs + 4] - R.shape.pts[3 * bs + 1],
+                        e2 = R.shape.pts[3 * bs + 5] - R.shape.pts[3 * bs + 2];
             const float L = sqrtf(e0 * e0 + e1 * e1 + e2 * e2);
             if (L > 0.f) { tl0 = e0 / L; tl1 = e1 / L; tl2 = e2 / L; }
         }
@@ -574,10 +703,11 @@ __device__ int rigid_region(const RigidCur& R, float3 x, float3& n, float3& t)
 // separating node (v_n >= 0), else v_rel' = c_d max(1 - mu_k |v_n| / |v_t|, 0) v_t
 // with v_t the tangential part (regular) or the part along the 1D tangent.
 // Returns whether the node was changed; dp = node momentum change.
+template <bool EXT>
 __device__ bool rigid_contact(const RigidCur& R, float3 x, float m, float3& v, float3& dp)
 {
     float3 n, t;
-    const int code = rigid_region(R, x, n, t);
+    const int code = rigid_region<EXT>(R, x, n, t);
     if (code == 0) return false;
     const float r0 = x.x - R.c[0], r1 = x.y - R.c[1], r2 = x.z - R.c[2];
     const float vr0 = R.vel[0] + R.omega[1] * r2 - R.omega[2] * r1;
@@ -611,6 +741,8 @@ __device__ void stage_rigid(const RigidDev& src, double t_now, RigidCur& dst)
 {
     dst.type = src.type;
     dst.n_pts = src.n_pts;
+    dst.n_tris = src.n_tris;
+    dst.n_spine = src.n_spine;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         dst.vel[i] = src.vel[i];
@@ -638,6 +770,7 @@ __device__ void flush_impulse(const StepArgs& a, const float* simp, int scene, i
 // Rigids of a scene are staged in shared memory (posed at the scene's clock).
 // Grid update of node nid of node brick B (Eq. 3, contact, walls), clearing
 // the P2G accumulator; rigid impulses are summed into simp (shared).
+template <bool EXT>
 __device__ __forceinline__ void grid_node(const StepArgs& a, int B, int scene, int nid, int lane, const RigidCur* rig,
                                           int nr, float* simp)
 {
@@ -658,7 +791,7 @@ __device__ __forceinline__ void grid_node(const StepArgs& a, int B, int scene, i
         const float3 xI = f3(gi * dxs, gj * dxs, gk * dxs);
         for (int r = 0; r < nr; ++r) {
             float3 dp;
-            if (rigid_contact(rig[r], xI, g.x, v, dp)) {
+            if (rigid_contact<EXT>(rig[r], xI, g.x, v, dp)) {
                 touched |= 1u << r;
                 dpr[r][0] = dp.x; dpr[r][1] = dp.y; dpr[r][2] = dp.z;
             }
@@ -704,6 +837,7 @@ __device__ __forceinline__ void grid_node(const StepArgs& a, int B, int scene, i
     }
 }
 
+template <bool EXT>
 __global__ void __launch_bounds__(kGridThreads, 4) k_grid(StepArgs a)
 {
     __shared__ RigidCur rig[kMaxRigids];
@@ -718,7 +852,7 @@ __global__ void __launch_bounds__(kGridThreads, 4) k_grid(StepArgs a)
         // no scene has a rigid: 4 node bricks per step, no staging, no barriers
         for (int base = blockIdx.x * 4; base < n_nact; base += gridDim.x * 4) {
             const int item = base + grp;
-            if (item < n_nact) grid_node(a, a.sb.nact_brick[item], a.sb.nact_scene[item], nid, lane, nullptr, 0, nullptr);
+            if (item < n_nact) grid_node<EXT>(a, a.sb.nact_brick[item], a.sb.nact_scene[item], nid, lane, nullptr, 0, nullptr);
         }
         return;
     }
@@ -750,11 +884,11 @@ __global__ void __launch_bounds__(kGridThreads, 4) k_grid(StepArgs a)
             }
             const int my_brick = my_scene >= 0 ? s_brk[item - c0] : 0;
             if (no_rigid) {
-                if (my_scene >= 0) grid_node(a, my_brick, my_scene, nid, lane, nullptr, 0, nullptr);
+                if (my_scene >= 0) grid_node<EXT>(a, my_brick, my_scene, nid, lane, nullptr, 0, nullptr);
                 continue;
             }
             if (staged) {
-                if (my_scene >= 0) grid_node(a, my_brick, my_scene, nid, lane, rig, s_nrig, simp);
+                if (my_scene >= 0) grid_node<EXT>(a, my_brick, my_scene, nid, lane, rig, s_nrig, simp);
                 continue;
             }
             if (nid == 0) s_scene[grp] = my_scene;
@@ -777,9 +911,12 @@ __global__ void __launch_bounds__(kGridThreads, 4) k_grid(StepArgs a)
                     const int nr = a.scenes[target].n_rigid;
                     const double t_now = a.t_scene[target];
                     if (tid < nr) stage_rigid(a.rigids[target * kMaxRigids + tid], t_now, rig[tid]);
-                    for (int t = tid; t < nr * kMaxPts * 3; t += kGridThreads) {
-                        const int r = t / (kMaxPts * 3), k = t % (kMaxPts * 3);
-                        rig[r].pts[k] = a.rigids[target * kMaxRigids + r].pts[k];
+                    constexpr int kShapeWords = (int)(sizeof(RigidShape) / sizeof(int));
+                    static_assert(sizeof(RigidShape) % sizeof(int) == 0, "shape copied in words");
+                    for (int t = tid; t < nr * kShapeWords; t += kGridThreads) {
+                        const int r = t / kShapeWords, k = t % kShapeWords;
+                        reinterpret_cast<int*>(&rig[r].shape)[k] =
+                            reinterpret_cast<const int*>(&a.rigids[target * kMaxRigids + r].shape)[k];
                     }
                     for (int t = tid; t < kMaxRigids * 6; t += kGridThreads) simp[t] = 0.f;
                     if (tid == 0) { s_staged = target; s_nrig = nr; }
@@ -787,7 +924,7 @@ __global__ void __launch_bounds__(kGridThreads, 4) k_grid(StepArgs a)
                 }
                 if (!done && my_scene == target) {
                     done = true;
-                    grid_node(a, my_brick, target, nid, lane, rig, s_nrig, simp);
+                    grid_node<EXT>(a, my_brick, target, nid, lane, rig, s_nrig, simp);
                 }
                 __syncthreads();
                 if (nid == 0 && my_scene == target) s_scene[grp] = -1;
@@ -1492,7 +1629,8 @@ int occupancy_p2g_std()
 
 cudaError_t launch_grid(const StepArgs& a, cudaStream_t s)
 {
-    k_grid<<<a.grid_ctas, kGridThreads, 0, s>>>(a);
+    if (a.rigid_ext) k_grid<true><<<a.grid_ctas, kGridThreads, 0, s>>>(a);
+    else k_grid<false><<<a.grid_ctas, kGridThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -1543,7 +1681,7 @@ cudaError_t launch_g2p2g(const StepArgs& a, cudaStream_t s)
 int occupancy_grid()
 {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_grid, kGridThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_grid<true>, kGridThreads, 0);
     return b;
 }
 

@@ -25,12 +25,14 @@ STATUS = {
 MEM_HOST, MEM_DEVICE = 0, 1
 MODELS = {"fixed_corotated": 0, "neo_hookean": 1}
 SOLVERS = {"mls": 0, "standard": 1, "pb": 2}
-RIGID_TYPES = {"sphere": 0, "box": 1, "quad_slicer": 2, "segments": 3, "none": -1}
+RIGID_TYPES = {"sphere": 0, "box": 1, "quad_slicer": 2, "segments": 3, "arc": 4, "mesh_slicer": 5, "none": -1}
 FIELD = {"x": 1, "v": 2, "C": 4, "F": 8, "order": 16, "impulse": 32}
 FIELD_SHAPE = {"x": (3,), "v": (3,), "C": (3, 3), "F": (3, 3), "order": ()}
 OPT = {"use_graphs": 1, "launch_mode": 2, "p2g_threads": 3, "g2p_threads": 4, "ctas_per_sm": 5, "graph_chunk": 6,
        "phase_timing": 7, "p2g_chunk": 8, "fused": 9, "g2p_regs64": 10}
 MAX_PTS = 64
+MAX_TRIS = 64
+MAX_SPINE = 16
 MAX_RIGIDS = 8
 EBIT = {"out_of_domain": 1, "nonfinite": 2, "inverted": 4, "timeout": 8, "internal": 16}
 
@@ -58,6 +60,8 @@ class mpm_rigid(ct.Structure):
         ("vel", ct.c_float * 3), ("omega", ct.c_float * 3), ("mu_k", ct.c_float), ("c_d", ct.c_float),
         ("margin", ct.c_float), ("radius", ct.c_float), ("half", ct.c_float * 3), ("thickness", ct.c_float),
         ("spine_radius", ct.c_float), ("points", (ct.c_float * 3) * MAX_PTS),
+        ("n_triangles", ct.c_int32), ("n_spine", ct.c_int32), ("triangles", (ct.c_int32 * 3) * MAX_TRIS),
+        ("spine", ct.c_int32 * MAX_SPINE),
     ]
 
 
@@ -238,6 +242,16 @@ def make_rigid(desc):
     for i, p in enumerate(pts):
         for d in range(3):
             r.points[i][d] = float(p[d])
+    tris = np.asarray(desc.get("tris", np.zeros((0, 3))), dtype=np.int32).reshape(-1, 3)
+    spine = np.asarray(desc.get("spine", []), dtype=np.int32).reshape(-1)
+    if len(tris) > MAX_TRIS or len(spine) > MAX_SPINE:
+        raise ValueError("too many mesh triangles or spine points")
+    r.n_triangles, r.n_spine = len(tris), len(spine)
+    for i, t in enumerate(tris):
+        for d in range(3):
+            r.triangles[i][d] = int(t[d])
+    for i, v in enumerate(spine):
+        r.spine[i] = int(v)
     return r
 
 

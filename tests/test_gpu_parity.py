@@ -5,6 +5,8 @@ identical FP32 inputs, at sizes the oracle finishes in seconds that still span
 many bricks and ragged (partially filled) bricks, plus the whole-run criterion
 on the elastic-cube workload and sampled checks at the full 1M-particle size.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -274,3 +276,48 @@ def test_push_out_matches_oracle(shape, steps_before):
     inside = [oracle.geometry(r, p)[3] for p in out["x"].astype(np.float64)]
     assert min(inside) > -1e-6
     assert np.sum(np.abs(inside) < 1e-6) > 20  # the pushed particles sit on the surface
+
+
+def _suturing_scene():
+    # Small tissue slab with a curved needle (Arc, Sec. IV-C) turning about its
+    # own circle axis, i.e. sliding along its tangent as in an insertion, and
+    # a curved blade given as a triangle mesh (TriangleMeshSlicer, Sec. IV-B)
+    # moving down into the tissue with its spine up.
+    n = 64
+    sc = W.tissue_slab(cells=(40, 8, 40), lo=(0.25, 0.15, 0.25), size=(0.5, 0.1, 0.5), n=n, substeps=40,
+                       with_tools=False)
+    dx = 1.0 / n
+    # needle: circle of radius 0.05 in a vertical plane, half of it below the top surface
+    qn = (math.cos(0.2), 0.0, math.sin(0.2), 0.0)  # plane turned about world y
+    needle = W.arc((0.37 + 0.31 * dx, 0.25 + 0.02 + 0.17 * dx, 0.41 - 0.23 * dx), qn, arc_radius=0.05, start=-2.6,
+                   sweep=2.2, radius=0.002, omega=(0.0, 0.0, 0.0), mu_k=0.3, c_d=1.0, margin=dx)
+    # its body z axis in world coordinates: turning about it moves the arc along its tangent
+    w, x, y, z = qn
+    axis = np.array([2 * (x * z + w * y), 2 * (y * z - w * x), 1 - 2 * (x * x + y * y)])
+    needle["omega"] = tuple(4.0 * axis)
+    pts, tris, spine = W.curved_blade_mesh(half_edge=0.07, depth=0.05, bend=0.015)
+    # blade: edge (body +y) pointing down, normal along world x, slightly turned
+    blade = W.mesh_slicer((0.62 + 0.37 * dx, 0.25 + 0.025 - 0.015 + 0.11 * dx, 0.58 + 0.21 * dx),
+                          (0.0, math.sqrt(0.5), 0.05, math.sqrt(0.5)), pts, tris, spine, thickness=0.003,
+                          spine_radius=0.002, vel=(0.0, -0.1, 0.02), mu_k=0.3, c_d=1.0, margin=dx)
+    q = np.array(blade["quat"])
+    blade["quat"] = tuple(q / np.linalg.norm(q))
+    sc["rigids"] = [needle, blade]
+    return sc
+
+
+@pytest.mark.parametrize("steps_before", [0, 10])
+def test_arc_needle_and_mesh_slicer_match_oracle(steps_before):
+    sc = _suturing_scene()
+    N = len(sc["x"])
+    g = np.random.default_rng(61)
+    v0 = (0.05 * g.normal(size=(N, 3))).astype(np.float32)
+    x, v, C, F, out = gpu_one_step(sc, v0, np.zeros((N, 3, 3), np.float32),
+                                   np.tile(np.eye(3, dtype=np.float32), (N, 1, 1)), steps_before=steps_before)
+    st, gm, gv, err, imp = oracle_one_step(sc, x, v, C, F, steps_before)
+    assert err == 0
+    check_fields(sc, out, st, Scales(sc, F))
+    check_grid(sc, out, gm, gv, Scales(sc, F))
+    for r in range(2):
+        assert np.abs(imp[r, :3]).max() > 0, r  # both tools are in contact
+        assert_close(f"impulse[{r}]", out["impulse"][r], imp[r], rtol=1e-4, rel_scale=1e-4)
