@@ -112,12 +112,22 @@ def test_adjoint_refuses_what_it_does_not_differentiate():
             sim.backward(np.zeros((len(sc["x"]), 3), np.float32))
 
 
+# Step of the single-coordinate differences.  Perturbing one particle changes
+# the 200-substep loss (~0.14) by only ~1e-8 h, while two FP64 runs whose
+# inputs differ round differently by ~1e-14 in the loss: at h = 1e-6 that
+# rounding is ~1 % of the difference (measured on the largest E coordinate:
+# -1.5737e-8 at h = 1e-6, -1.5593e-8 at 1e-5, -1.5589e-8 at 1e-4, -1.5572e-8 at
+# 1e-3, against -1.5571e-8 from the adjoint).  h = 1e-3 of each coordinate's
+# own size keeps that rounding near 1e-4 and the O(h^2) truncation near 1e-6.
+H_COORD = 1e-3
+
+
 def test_adjoint_full_size_single_coordinates():
     # The differentiable workload at full size (32,768 particles, 64^3, 200
-    # substeps, a checkpoint every 20): single coordinates of E (relative step),
-    # nu and the three components of v0 on a seeded sample of particles plus the
-    # particle of largest |E dL/dE|, each against its own FP64 central
-    # difference (the oracle runs in spawned worker processes).
+    # substeps, a checkpoint every 20): single coordinates of E, nu and the
+    # three components of v0 on a seeded sample of particles plus the particle
+    # of largest |E dL/dE|, each against its own FP64 central difference (the
+    # oracle runs in spawned worker processes).
     from tests.oracle_pool import diff_cube_loss, map_tasks
 
     sc = W.diff_cube()
@@ -127,12 +137,20 @@ def test_adjoint_full_size_single_coordinates():
     g = np.random.default_rng(11)
     idx = [int(i) for i in g.choice(N, 3, replace=False)] + [int(np.argmax(np.abs(gE * sc["E"])))]
     coords = [("E", 0), ("nu", 0), ("v0", 0), ("v0", 1), ("v0", 2)]
-    tasks = [({}, steps, [(k, i, d, s * H)]) for i in idx for k, d in coords for s in (1, -1)]
+
+    def step(k, i, d):  # E: relative; nu, v0: absolute, scaled by the coordinate
+        if k == "E":
+            return H_COORD
+        if k == "nu":
+            return H_COORD * float(sc["nu"][i])
+        return H_COORD * max(abs(float(sc["v"][i, d])), 0.1)
+
+    tasks = [({}, steps, [(k, i, d, s * step(k, i, d))]) for i in idx for k, d in coords for s in (1, -1)]
     losses = np.array(map_tasks(diff_cube_loss, tasks)).reshape(len(idx), len(coords), 2)
     scale = {"E": np.abs(gE * sc["E"]).max(), "nu": np.abs(gnu).max(), "v0": np.abs(gv0).max()}
     for a, i in enumerate(idx):
         for b, (k, d) in enumerate(coords):
-            fd = (losses[a, b, 0] - losses[a, b, 1]) / (2 * H)
+            fd = (losses[a, b, 0] - losses[a, b, 1]) / (2 * step(k, i, d))
             got = {"E": gE[i] * sc["E"][i], "nu": gnu[i], "v0": gv0[i, d]}[k]
             print(f"particle {i} {k}[{d}]: adjoint {got:.6e} fd {fd:.6e}")
             assert abs(got - fd) <= TOL * abs(fd) + 1e-6 * scale[k], (i, k, d, got, fd)
@@ -188,8 +206,10 @@ def test_adjoint_dot_product_per_block(model, steps):
         sim.substep(sc["dt"], steps)
         ws = {b: g.normal(size=base[b].shape) for b in OUT_BLOCKS}
         jt = {b: sim.backward_state({b: ws[b]}) for b in OUT_BLOCKS}
-    # oracle: J u by central differences, one direction per input block
-    steps_h = {"x": 1e-6, "v": 1e-6, "C": 1e-5, "F": 1e-6}
+    # oracle: J u by central differences, one direction per input block (the
+    # Lame parameters with a relative step of 1e-3: the x block of their
+    # response is ~dt times smaller than the FP64 rounding of x / 1e-6)
+    steps_h = {"x": 1e-6, "v": 1e-6, "C": 1e-5, "F": 1e-6, "mu": 1e-3, "lam": 1e-3}
     worst = 0.0
     for a in IN_BLOCKS:
         u = g.normal(size=base[a].shape)
