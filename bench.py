@@ -539,23 +539,35 @@ def run_scale_sweep(stream):
 
 
 def run_paper_timing(stream):
-    """The paper's timing scene (Sec. III-D): a cube falling on the fixed 56^3 grid,
-    steps of 10 substeps x 0.002 s; 15 steps (through the impact) per particle
-    count, graph replay timed with CUDA events after 2 steps of warm-up."""
+    """The paper's timing scene (Sec. III-D): a cube falling on the fixed 56^3
+    grid, each step advancing 0.02 s; MLS-MPM and standard MPM take 10 substeps
+    of 0.002 s per step, PB-MPM one step of 0.02 s with 10 or 20 cycles.  For
+    each particle count and solver: 15 steps (through the impact) timed with
+    CUDA events after 2 steps of warm-up, graph replay."""
     from paper_2502_18437_gb300 import mpm, workloads
 
+    per = workloads.PAPER_TIMING_SUBSTEPS_PER_STEP
+    solvers = (("mls", {}, per), ("standard", {}, per), ("pb10", {"solver": "pb", "pb_iterations": 10}, 1),
+               ("pb20", {"solver": "pb", "pb_iterations": 20}, 1))
     out = {}
     for N in workloads.PAPER_TIMING_POINTS:
         sc = workloads.paper_timing_cube(N=N)
-        sim = mpm.from_workload(sc, stream=stream.cuda_stream)
-        dt, per = sc["dt"], workloads.PAPER_TIMING_SUBSTEPS_PER_STEP
-        sim.substep(dt, 2 * per)
-        ms = time_substeps(sim, stream, dt, 15 * per)
-        bits = sim.error_bits(0)
-        sim.close()
-        out[str(N)] = {"steps_per_s": 15 / (ms / 1e3), "particle_substeps_per_s": N * 15 * per / (ms / 1e3),
-                       "ms_per_step": ms / 15, "error_bits": bits}
-    return {"grid": "56^3", "step": "0.02 s = 10 substeps of 0.002 s", "points": out,
+        row = {}
+        for name, kw, substeps in solvers:
+            kw = dict(kw)
+            if name == "standard":
+                kw["solver"] = "standard"
+            sim = mpm.from_workload(sc, stream=stream.cuda_stream, **kw)
+            dt = sc["dt"] * per / substeps
+            sim.substep(dt, 2 * substeps)
+            ms = time_substeps(sim, stream, dt, 15 * substeps)
+            bits = sim.error_bits(0)
+            sim.close()
+            row[name] = {"steps_per_s": 15 / (ms / 1e3), "ms_per_step": ms / 15,
+                         "particle_steps_per_s": N * 15 / (ms / 1e3), "error_bits": bits}
+        out[str(N)] = row
+    return {"grid": "56^3", "step": "0.02 s: 10 substeps of 0.002 s (mls, standard) or one PB-MPM step "
+            "of 0.02 s with 10 / 20 cycles", "points": out,
             "paper": "figure only (absent from the text): no number to compare"}
 
 
