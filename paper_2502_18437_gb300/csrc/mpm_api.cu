@@ -179,11 +179,13 @@ StepArgs step_args(mpm_ctx* c, float dt, int s0, int s1, const PState& in, const
     }
     a.any_rigid = 0;
     a.rigid_ext = 0;
+    a.any_solid = 0;
     for (int sc = s0; sc < s1; ++sc) {
         if (c->h_scenes[sc].n_rigid > 0) a.any_rigid = 1;
         for (int k = 0; k < kMaxRigids; ++k) {
             const int ty = c->rigid_type[(size_t)sc * kMaxRigids + k];
             if (ty == MPM_ARC || ty == MPM_MESH_SLICER) a.rigid_ext = 1;
+            if (ty == MPM_SPHERE || ty == MPM_BOX) a.any_solid = 1;
         }
     }
     return a;

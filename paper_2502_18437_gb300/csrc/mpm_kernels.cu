@@ -1230,7 +1230,7 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_g2p2g(StepArgs a)
         if (!walker_next(a, n_act, vw, bar, s_item, work, buf, phase, item)) break;
         const int start = a.sb.act_start[item], count = a.sb.act_count[item], scene = a.sb.act_scene[item];
         const SceneDev sc = a.scenes[scene];
-        const int n_solid = a.any_rigid ? sc.n_rigid : 0;
+        const int n_solid = a.any_solid ? sc.n_rigid : 0;
         if (n_solid && scene != s_pose_scene) stage_solids(a, scene, s_pose);
         const int n = sc.n, nb = sc.nb, lb = a.sb.act_brick[item] - sc.brick_base;
         const int ox = (lb / (nb * nb)) * 4, oy = ((lb / nb) % nb) * 4, oz = (lb % nb) * 4;
@@ -1658,13 +1658,15 @@ static void launch_g2p_variant(const StepArgs& a, cudaStream_t s)
 cudaError_t launch_g2p(const StepArgs& a, cudaStream_t s)
 {
     const int c = a.persistent_ctas;
+    // the push-out variant only where a scene has a solid shape: blades, needles and
+    // segments push nothing out
     if (a.solver == MPM_SOLVER_STANDARD) {
-        if (a.any_rigid) k_g2p<128, 8, kG2PStdGrad | kG2PSolids><<<c, 128, 0, s>>>(a);
+        if (a.any_solid) k_g2p<128, 8, kG2PStdGrad | kG2PSolids><<<c, 128, 0, s>>>(a);
         else k_g2p<128, 8, kG2PStdGrad><<<c, 128, 0, s>>>(a);
     } else if (a.solver == MPM_SOLVER_PB) {
-        if (a.any_rigid) k_g2p<128, 8, kG2PNoStress | kG2PSolids><<<c, 128, 0, s>>>(a);
+        if (a.any_solid) k_g2p<128, 8, kG2PNoStress | kG2PSolids><<<c, 128, 0, s>>>(a);
         else k_g2p<128, 8, kG2PNoStress><<<c, 128, 0, s>>>(a);
-    } else if (a.any_rigid) {
+    } else if (a.any_solid) {
         launch_g2p_variant<kG2PSolids>(a, s);
     } else {
         launch_g2p_variant<0>(a, s);

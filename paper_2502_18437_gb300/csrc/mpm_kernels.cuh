@@ -60,6 +60,7 @@ struct StepArgs {
     int tau_valid;               // P2G reads the stored stress (else recomputes it from F)
     int any_rigid;               // some scene of the range has a rigid (contact in the grid update)
     int rigid_ext;               // some scene of the range has an arc or a mesh slicer
+    int any_solid;               // some scene of the range has a sphere or a box (particle push-out)
     int cell_order;              // P2G rewrites each pass's permutation slots in cell order
     int solver;                  // MPM_SOLVER_*
     float pb_beta;               // PB-MPM constraint blend
