@@ -257,7 +257,9 @@ __global__ void __launch_bounds__(kAdjThreads) k_g2p_adj(AdjArgs q)
         const int start = a.sb.act_start[item], count = a.sb.act_count[item];
         const SceneDev sc = a.scenes[a.sb.act_scene[item]];
         const int n = sc.n, nb = sc.nb, lb = a.sb.act_brick[item] - sc.brick_base;
-        const int ox = (lb / (nb * nb)) * 4, oy = ((lb / nb) % nb) * 4, oz = (lb % nb) * 4;
+        int ox, oy, oz;
+        brick_coords(nb, sc.nb_log2, lb, ox, oy, oz);
+        ox *= 4; oy *= 4; oz *= 4;
         const float fn = (float)n, dt = a.dt, c4 = 4.f * fn;
         const float4* win = vw[buf];
         for (int k = tid; k < count; k += kAdjThreads) {
@@ -377,9 +379,11 @@ __global__ void __launch_bounds__(256) k_grid_adj(StepArgs a)
         const int B = a.sb.nact_brick[item];
         const SceneDev sc = a.scenes[a.sb.nact_scene[item]];
         const int n = sc.n, nb = sc.nb, lb = B - sc.brick_base;
-        const int gi = (lb / (nb * nb)) * 4 + (nid >> 4);
-        const int gj = ((lb / nb) % nb) * 4 + ((nid >> 2) & 3);
-        const int gk = (lb % nb) * 4 + (nid & 3);
+        int bx, by, bz;
+        brick_coords(nb, sc.nb_log2, lb, bx, by, bz);
+        const int gi = bx * 4 + (nid >> 4);
+        const int gj = by * 4 + ((nid >> 2) & 3);
+        const int gk = bz * 4 + (nid & 3);
         const int node = B * 64 + nid;
         const float4 vb = a.G[node];
         const float4 vm = a.V[node];
@@ -431,7 +435,9 @@ __global__ void __launch_bounds__(kAdjThreads) k_p2g_adj(AdjArgs q)
         const int scene = a.sb.act_scene[item];
         const SceneDev sc = a.scenes[scene];
         const int n = sc.n, nb = sc.nb, lb = a.sb.act_brick[item] - sc.brick_base;
-        const int ox = (lb / (nb * nb)) * 4, oy = ((lb / nb) % nb) * 4, oz = (lb % nb) * 4;
+        int ox, oy, oz;
+        brick_coords(nb, sc.nb_log2, lb, ox, oy, oz);
+        ox *= 4; oy *= 4; oz *= 4;
         const float fn = (float)n, dxs = 1.f / fn, m = sc.m_p;
         const float kA = a.dt * sc.V0 * 4.f * fn * fn;
         const float4* win = vw[buf];

@@ -390,6 +390,9 @@ extern "C" int mpm_create(const mpm_config* cfg, void* stream, mpm_ctx** out)
         d.nb = d.n / 4;
         d.brick_base = c->brick_base[s];
         d.tile_base = c->tile_base[s];
+        d.nb_log2 = -1;
+        for (int k = 0; k < 31; ++k)
+            if ((1 << k) == d.nb) d.nb_log2 = k;
     }
     c->h_rigids.assign((size_t)c->n_scenes * kMaxRigids, RigidDev{});
     c->rigid_type.assign((size_t)c->n_scenes * kMaxRigids, MPM_RIGID_NONE);

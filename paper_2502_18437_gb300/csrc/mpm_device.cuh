@@ -37,7 +37,23 @@ struct SceneDev {
     int tile_base;   // first scan tile of the scene (tiles never straddle scenes)
     float m_p, V0;   // particle mass and initial volume
     float mu, lam;   // uniform Lame parameters (pp_mat == 0)
+    int nb_log2;     // log2(nb) when nb is a power of two, else -1
 };
+
+// Coordinates (bx, by, bz) of the scene-local brick lb = (bx nb + by) nb + bz:
+// shifts for power-of-two grids, divisions otherwise.
+__device__ __forceinline__ void brick_coords(int nb, int nb_log2, int lb, int& bx, int& by, int& bz)
+{
+    if (nb_log2 >= 0) {
+        bx = lb >> (2 * nb_log2);
+        by = (lb >> nb_log2) & (nb - 1);
+        bz = lb & (nb - 1);
+    } else {
+        bx = lb / (nb * nb);
+        by = (lb / nb) % nb;
+        bz = lb % nb;
+    }
+}
 
 constexpr int kMaxTris = MPM_MAX_MESH_TRIANGLES;
 constexpr int kMaxSpine = MPM_MAX_SPINE_POINTS;

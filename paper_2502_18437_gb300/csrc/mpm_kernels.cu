@@ -313,7 +313,9 @@ __global__ void __launch_bounds__(kP2GThreads, 4) k_p2g(StepArgs a)
         const int scene = a.sb.act_scene[item];
         const SceneDev sc = a.scenes[scene];
         const int n = sc.n, nb = sc.nb, lb = b - sc.brick_base;
-        const int ox = (lb / (nb * nb)) * 4, oy = ((lb / nb) % nb) * 4, oz = (lb % nb) * 4;
+        int ox, oy, oz;
+        brick_coords(nb, sc.nb_log2, lb, ox, oy, oz);
+        ox *= 4; oy *= 4; oz *= 4;
         const float fn = (float)n, dxs = 1.0f / fn;
         const float m = sc.m_p;
         const float kA = a.dt * sc.V0 * 4.0f * fn * fn;
@@ -621,7 +623,10 @@ __device__ int rigid_region(const RigidCur& R, float3 x, float3& n, float3& t)
             else if (q1 >= q2) nl1 = p1 >= 0.f ? 1.f : -1.f;
             else nl2 = p2 >= 0.f ? 1.f : -1.f;
         }
-    } else if (R.type == MPM_QUAD_SLICER) {
+    } else if (R.type == MPM_QUAD_SLICER &&
+               fabsf(p2) < (fmaxf(0.5f * R.thickness, R.spine_radius) + R.margin) * 1.000001f + 1e-30f) {
+        // (beyond that distance from the blade plane neither the spine nor the faces
+        // can hold the node: both distances are at least |p2|)
         const float A = R.half[0], Bh = R.half[1];
         const float es = fmaxf(fabsf(p0) - A, 0.f), et = p1 + Bh;
         const float dsp = sqrtf(es * es + et * et + p2 * p2);
@@ -775,10 +780,12 @@ __device__ __forceinline__ void grid_node(const StepArgs& a, int B, int scene, i
                                           int nr, float* simp)
 {
     const SceneDev sc = a.scenes[scene];
-    const int n = sc.n, nb = sc.nb, lb = B - sc.brick_base;
-    const int gi = (lb / (nb * nb)) * 4 + (nid >> 4);
-    const int gj = ((lb / nb) % nb) * 4 + ((nid >> 2) & 3);
-    const int gk = (lb % nb) * 4 + (nid & 3);
+    const int n = sc.n, lb = B - sc.brick_base;
+    int bx, by, bz;
+    brick_coords(sc.nb, sc.nb_log2, lb, bx, by, bz);
+    const int gi = bx * 4 + (nid >> 4);
+    const int gj = by * 4 + ((nid >> 2) & 3);
+    const int gk = bz * 4 + (nid & 3);
     const int node = B * 64 + nid;
     const float4 g = a.G[node];
     a.G[node] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1143,7 +1150,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_g2p(StepArgs a)
         const int n_solid = SOLIDS ? sc.n_rigid : 0;
         if (n_solid && scene != s_pose_scene) stage_solids(a, scene, s_pose);
         const int nb = sc.nb, lb = a.sb.act_brick[item] - sc.brick_base;
-        const int ox = (lb / (nb * nb)) * 4, oy = ((lb / nb) % nb) * 4, oz = (lb % nb) * 4;
+        int ox, oy, oz;
+        brick_coords(nb, sc.nb_log2, lb, ox, oy, oz);
+        ox *= 4; oy *= 4; oz *= 4;
         // the brick's first particle of each thread: its copies start here (the
         // thread's last call of the previous brick has read both buffers)
         int pcur = tid < count ? a.sb.perm[start + tid] : -1;
@@ -1233,7 +1242,9 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_g2p2g(StepArgs a)
         const int n_solid = a.any_solid ? sc.n_rigid : 0;
         if (n_solid && scene != s_pose_scene) stage_solids(a, scene, s_pose);
         const int n = sc.n, nb = sc.nb, lb = a.sb.act_brick[item] - sc.brick_base;
-        const int ox = (lb / (nb * nb)) * 4, oy = ((lb / nb) % nb) * 4, oz = (lb % nb) * 4;
+        int ox, oy, oz;
+        brick_coords(nb, sc.nb_log2, lb, ox, oy, oz);
+        ox *= 4; oy *= 4; oz *= 4;
         const float fn = (float)n, dxs = 1.0f / fn;
         const float m = sc.m_p;
         const float kA = a.dt * sc.V0 * 4.0f * fn * fn;
@@ -1365,7 +1376,9 @@ __global__ void __launch_bounds__(kStdThreads) k_p2g_std(StepArgs a)
         const int scene = a.sb.act_scene[item];
         const SceneDev sc = a.scenes[scene];
         const int n = sc.n, nb = sc.nb, lb = b - sc.brick_base;
-        const int ox = (lb / (nb * nb)) * 4, oy = ((lb / nb) % nb) * 4, oz = (lb % nb) * 4;
+        int ox, oy, oz;
+        brick_coords(nb, sc.nb_log2, lb, ox, oy, oz);
+        ox *= 4; oy *= 4; oz *= 4;
         const float fn = (float)n, m = sc.m_p;
         const float kap = a.dt * sc.V0 * fn;  // dt V0 times the n of grad W = n dW/df
         unsigned ebits = 0;
@@ -1451,7 +1464,9 @@ __global__ void __launch_bounds__(kVcThreads) k_g2p_vc(StepArgs a)
         const int start = a.sb.act_start[item], count = a.sb.act_count[item];
         const SceneDev sc = a.scenes[a.sb.act_scene[item]];
         const int n = sc.n, nb = sc.nb, lb = a.sb.act_brick[item] - sc.brick_base;
-        const int ox = (lb / (nb * nb)) * 4, oy = ((lb / nb) % nb) * 4, oz = (lb % nb) * 4;
+        int ox, oy, oz;
+        brick_coords(nb, sc.nb_log2, lb, ox, oy, oz);
+        ox *= 4; oy *= 4; oz *= 4;
         const float c4 = 4.0f * (float)n;
         linearize_window<kVcThreads>(vw[buf], lin);
         __syncthreads();

@@ -114,7 +114,8 @@ __device__ __forceinline__ int aggregated_rank_mark(const SortBufs& sb, const Sc
             if (base == 0) {
                 atomicAdd(&ts[lb >> sb.tile_shift].y, 1);
                 const int nb = sc.nb;
-                const int bx = lb / (nb * nb), by = (lb / nb) % nb, bz = lb % nb;
+                int bx, by, bz;
+                brick_coords(nb, sc.nb_log2, lb, bx, by, bz);
 #pragma unroll
                 for (int o = 0; o < 8; ++o) {
                     const int ex = bx + (o >> 2), ey = by + ((o >> 1) & 1), ez = bz + (o & 1);
@@ -404,7 +405,8 @@ __device__ __forceinline__ void issue_halo(const StepArgs& a, int item, float4* 
     const int b = a.sb.act_brick[item];
     const SceneDev& sc = a.scenes[a.sb.act_scene[item]];
     const int nb = sc.nb, lb = b - sc.brick_base;
-    const int bx = lb / (nb * nb), by = (lb / nb) % nb, bz = lb % nb;
+    int bx, by, bz;
+    brick_coords(nb, sc.nb_log2, lb, bx, by, bz);
     fence_proxy_async();
     unsigned bytes = 0;
 #pragma unroll
