@@ -162,11 +162,13 @@ StepArgs step_args(mpm_ctx* c, float dt, int s0, int s1, const PState& in, const
     int& op = c->occ_p2g[c->p2g_chunk / kP2GThreads - 2];
     if (!op) op = std::max(1, occupancy_p2g(c->p2g_chunk));
     if (!c->occ_grid) c->occ_grid = std::max(1, occupancy_grid());
+    if (!c->occ_grid_plain) c->occ_grid_plain = std::max(1, occupancy_grid_plain());
     if (!c->occ_fused) c->occ_fused = std::max(1, occupancy_g2p2g());
     a.persistent_ctas = c->num_sms * cap_occ(c, og);
     a.g2p_regs64 = c->g2p_regs64;
     a.p2g_ctas = c->num_sms * cap_occ(c, op);
     a.grid_ctas = c->num_sms * c->occ_grid;
+    a.grid_plain_ctas = c->num_sms * c->occ_grid_plain;
     a.fused_ctas = c->num_sms * cap_occ(c, c->occ_fused);
     a.p2g_chunk = c->p2g_chunk;
     a.g2p_threads = c->g2p_threads;

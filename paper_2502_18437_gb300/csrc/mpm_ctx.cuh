@@ -68,6 +68,7 @@ struct mpm_ctx {
     int occ_g2p[2][3] = {};
     int occ_p2g[3] = {};
     int occ_grid = 0;
+    int occ_grid_plain = 0;
     int occ_fused = 0;
     int occ_p2g_std = 0;
     std::vector<cudaEvent_t> phase_events;  // 5 per timed substep

@@ -175,21 +175,40 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(StepArgs a)
 // Counting-sort scatter; also clears the range's tile sums for the next
 // substep (the scan has read them).  write_perm = 0 only clears (the adjoint
 // reuses a recorded permutation).
-__global__ void k_scatter(StepArgs a, int write_perm)
+// Each thread takes kScatterPer particles, 256 apart, with their loads issued
+// together (a 1M-particle range in one wave of CTAs).
+__global__ void __launch_bounds__(256) k_scatter(StepArgs a, int write_perm)
 {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = a.r.p0 + g;
-    if (write_perm && g < a.r.np) {
-        const int key = a.sb.key[i], brick = key >> 6;
-        const int dst = (brick >= a.r.bb0 && brick < a.r.bb0 + a.r.nbr) ? __ldg(&a.sb.off[brick]) + a.sb.rank[i] : -1;
-        if (dst >= a.r.p0 && dst < a.r.p0 + a.r.np) {
-            a.sb.perm[dst] = i;
-            a.sb.scell[dst] = (unsigned char)(key & 63);
-        } else {
-            atomicOr(&a.err[a.r.s0], MPM_EBIT_INTERNAL);
+    const int g0 = blockIdx.x * (256 * kScatterPer) + threadIdx.x;
+    int key[kScatterPer], rank[kScatterPer], dst[kScatterPer];
+#pragma unroll
+    for (int u = 0; u < kScatterPer; ++u) {
+        const int g = g0 + u * 256;
+        key[u] = -1;
+        rank[u] = 0;
+        if (write_perm && g < a.r.np) {
+            key[u] = a.sb.key[a.r.p0 + g];
+            rank[u] = a.sb.rank[a.r.p0 + g];
         }
     }
-    if (g < a.r.nt) a.sb.tile_sum[a.r.t0 + g] = make_int4(0, 0, 0, 0);
+#pragma unroll
+    for (int u = 0; u < kScatterPer; ++u) {
+        const int brick = key[u] >> 6;
+        dst[u] = (key[u] >= 0 && brick >= a.r.bb0 && brick < a.r.bb0 + a.r.nbr) ? __ldg(&a.sb.off[brick]) + rank[u] : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < kScatterPer; ++u) {
+        const int g = g0 + u * 256;
+        if (write_perm && g < a.r.np) {
+            if (dst[u] >= a.r.p0 && dst[u] < a.r.p0 + a.r.np) {
+                a.sb.perm[dst[u]] = a.r.p0 + g;
+                a.sb.scell[dst[u]] = (unsigned char)(key[u] & 63);
+            } else {
+                atomicOr(&a.err[a.r.s0], MPM_EBIT_INTERNAL);
+            }
+        }
+        if (g < a.r.nt) a.sb.tile_sum[a.r.t0 + g] = make_int4(0, 0, 0, 0);
+    }
 }
 
 // Keys and ranks of the stored particles after the host changed positions
@@ -841,6 +860,19 @@ __device__ __forceinline__ void grid_node(const StepArgs& a, int B, int scene, i
             for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
             if (lane == 0) atomicAdd(&simp[r * 6 + c], x);
         }
+    }
+}
+
+// Grid update of a launch whose scenes have no rigid: no staging and no impulse
+// sums, so a budget of 32 registers holds twice the resident CTAs of k_grid and
+// the node bricks of a 1M-particle block are taken in one round.
+__global__ void __launch_bounds__(kGridThreads, 8) k_grid_plain(StepArgs a)
+{
+    const int tid = threadIdx.x, lane = tid & 31, grp = tid >> 6, nid = tid & 63;
+    const int n_nact = a.sb.counters[CTR_N_NACT];
+    for (int base = blockIdx.x * 4; base < n_nact; base += gridDim.x * 4) {
+        const int item = base + grp;
+        if (item < n_nact) grid_node<false>(a, a.sb.nact_brick[item], a.sb.nact_scene[item], nid, lane, nullptr, 0, nullptr);
     }
 }
 
@@ -1586,7 +1618,7 @@ cudaError_t launch_sort(const StepArgs& a, cudaStream_t s, bool write_perm)
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int work = a.r.np > a.r.nt ? a.r.np : a.r.nt;
-    k_scatter<<<n_blocks(work, 256), 256, 0, s>>>(a, write_perm ? 1 : 0);
+    k_scatter<<<n_blocks(work, 256 * kScatterPer), 256, 0, s>>>(a, write_perm ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -1644,7 +1676,8 @@ int occupancy_p2g_std()
 
 cudaError_t launch_grid(const StepArgs& a, cudaStream_t s)
 {
-    if (a.rigid_ext) k_grid<true><<<a.grid_ctas, kGridThreads, 0, s>>>(a);
+    if (!a.any_rigid) k_grid_plain<<<a.grid_plain_ctas, kGridThreads, 0, s>>>(a);
+    else if (a.rigid_ext) k_grid<true><<<a.grid_ctas, kGridThreads, 0, s>>>(a);
     else k_grid<false><<<a.grid_ctas, kGridThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -1699,6 +1732,13 @@ int occupancy_grid()
 {
     int b = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_grid<true>, kGridThreads, 0);
+    return b;
+}
+
+int occupancy_grid_plain()
+{
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_grid_plain, kGridThreads, 0);
     return b;
 }
 

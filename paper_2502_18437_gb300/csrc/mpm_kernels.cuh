@@ -55,6 +55,7 @@ struct StepArgs {
     float yield_stress;
     int persistent_ctas;         // CTAs of the persistent G2P kernel
     int p2g_ctas, grid_ctas;     // CTAs of the persistent P2G and grid kernels
+    int grid_plain_ctas;         // CTAs of the grid kernel of launches without rigids
     int fused_ctas;              // CTAs of the fused G2P + P2G kernel
     int p2g_chunk, g2p_threads, g2p_regs64;
     int tau_valid;               // P2G reads the stored stress (else recomputes it from F)
@@ -71,6 +72,7 @@ constexpr int kP2GThreads = 192;  // 64 cells x 3 node slices
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 4;
 constexpr int kScanChunk = kScanThreads * kScanItems;  // bricks per pass of a scan CTA
+constexpr int kScatterPer = 4;  // particles per thread of the counting-sort scatter
 
 cudaError_t launch_prepare(const StepArgs& a, const PState& st, cudaStream_t s);
 cudaError_t launch_sort(const StepArgs& a, cudaStream_t s, bool write_perm = true);
@@ -84,6 +86,7 @@ int occupancy_p2g_std();
 cudaError_t launch_g2p2g(const StepArgs& a, cudaStream_t s);
 int occupancy_g2p2g();
 int occupancy_grid();
+int occupancy_grid_plain();
 
 // state I/O helpers
 cudaError_t launch_gather_field(const PState& st, int cap, int p0, int np, int field, void* dst,
