@@ -26,22 +26,28 @@ namespace mpm {
 // particle's 3-node stencil reaches at most 2 nodes beyond its base cell, i.e.
 // into the next brick.  The key producers (G2P, k_prepare) count particles per
 // brick, flag those node bricks when the first particles enter a brick, and add
-// each tile's three totals as they go.  So every CTA of the scan (one per tile
-// of the range) knows its exclusive prefix from the tile totals before it,
+// each tile's totals as they go.  So every CTA of the scan (one per tile of
+// the range) knows its exclusive prefix from the tile totals before it,
 // without waiting for another CTA; a tile with no active node brick has
-// nothing to write and returns at once.
+// nothing to write and returns at once.  The active particle-brick list holds
+// the bricks of at least kBigBrick particles first (in brick order), then the
+// others: the fourth tile total counts the former, and the grand total of the
+// range places the latter.
 
-__device__ __forceinline__ int4 add4(int4 a, int4 b) { return make_int4(a.x + b.x, a.y + b.y, a.z + b.z, 0); }
+__device__ __forceinline__ int4 add4(int4 a, int4 b) { return make_int4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
 
 __device__ __forceinline__ int4 shfl_up4(int4 v, int d)
 {
-    return make_int4(__shfl_up_sync(kFull, v.x, d), __shfl_up_sync(kFull, v.y, d), __shfl_up_sync(kFull, v.z, d), 0);
+    return make_int4(__shfl_up_sync(kFull, v.x, d), __shfl_up_sync(kFull, v.y, d), __shfl_up_sync(kFull, v.z, d),
+                     __shfl_up_sync(kFull, v.w, d));
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan(StepArgs a)
 {
     __shared__ int4 s_warp[kScanThreads / 32];
+    __shared__ int s_wtot[kScanThreads / 32];
     __shared__ int4 s_prefix;
+    __shared__ int s_big_total;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const SortBufs& sb = a.sb;
     const int tile = a.r.t0 + blockIdx.x;
@@ -54,22 +60,38 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(StepArgs a)
     const int4 own = __ldcg(&sb.tile_sum[tile]);
     if (own.z == 0 && !last) return;  // no active node brick (hence no particle) here
 
-    // exclusive prefix: the totals of the range's tiles before this one
+    // exclusive prefix: the totals of the range's tiles before this one; and the
+    // range's count of big bricks (the start of the small bricks in the list)
     int4 pre = make_int4(0, 0, 0, 0);
-    for (int t = a.r.t0 + tid; t < tile; t += kScanThreads) pre = add4(pre, __ldcg(&sb.tile_sum[t]));
+    int wtot = 0;
+    for (int t = a.r.t0 + tid; t < a.r.t0 + a.r.nt; t += kScanThreads) {
+        const int4 ts = __ldcg(&sb.tile_sum[t]);
+        if (t < tile) pre = add4(pre, ts);
+        wtot += ts.w;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         pre.x += __shfl_xor_sync(kFull, pre.x, o);
         pre.y += __shfl_xor_sync(kFull, pre.y, o);
         pre.z += __shfl_xor_sync(kFull, pre.z, o);
+        pre.w += __shfl_xor_sync(kFull, pre.w, o);
+        wtot += __shfl_xor_sync(kFull, wtot, o);
     }
-    if (lane == 0) s_warp[warp] = pre;
+    if (lane == 0) {
+        s_warp[warp] = pre;
+        s_wtot[warp] = wtot;
+    }
     __syncthreads();
     if (tid == 0) {
         int4 p = make_int4(0, 0, 0, 0);
+        int wt = 0;
 #pragma unroll
-        for (int w = 0; w < kScanThreads / 32; ++w) p = add4(p, s_warp[w]);
+        for (int w = 0; w < kScanThreads / 32; ++w) {
+            p = add4(p, s_warp[w]);
+            wt += s_wtot[w];
+        }
         s_prefix = p;
+        s_big_total = wt;
         if (last) {
             const int4 tot = add4(p, own);
             if (tot.x == a.r.np) {
@@ -86,6 +108,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(StepArgs a)
     __syncthreads();
     if (own.z == 0) return;
     int4 run = s_prefix;
+    const int big_total = s_big_total;
 
     // scene of the tile
     int s;
@@ -105,7 +128,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(StepArgs a)
     for (int chunk = b0; chunk < b1; chunk += kScanChunk) {
         const int first = chunk + tid * kScanItems;
         int c[kScanItems];
-        unsigned pf = 0, nf = 0;
+        unsigned pf = 0, nf = 0, bf = 0;
         int4 local = make_int4(0, 0, 0, 0);
 #pragma unroll
         for (int k = 0; k < kScanItems; ++k) {
@@ -116,12 +139,14 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(StepArgs a)
                 const int flag = __ldcg(&sb.nflag[b]);
                 if (flag) sb.nflag[b] = 0;  // consumed
                 if (c[k] > 0) pf |= 1u << k;
+                if (c[k] >= kBigBrick) bf |= 1u << k;
                 if (flag) nf |= 1u << k;  // a non-empty brick always flags itself
                 local.x += c[k];
             }
         }
         local.y = __popc(pf);
         local.z = __popc(nf);
+        local.w = __popc(bf);
         // block exclusive scan of (particles, pbricks, nbricks)
         int4 incl = local;
 #pragma unroll
@@ -141,11 +166,13 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(StepArgs a)
             if (lane < kScanThreads / 32) s_warp[lane] = w;  // inclusive over warps
         }
         __syncthreads();
-        int4 excl = make_int4(incl.x - local.x, incl.y - local.y, incl.z - local.z, 0);
+        int4 excl = make_int4(incl.x - local.x, incl.y - local.y, incl.z - local.z, incl.w - local.w);
         if (warp > 0) excl = add4(excl, s_warp[warp - 1]);
         excl = add4(excl, run);
-        int po = a.r.p0 + excl.x, pi = excl.y, ni = excl.z;
-        if (pi + local.y > a.r.nbr || ni + local.z > a.r.nbr) {  // tile sums out of step with the bricks
+        // list positions: big bricks from excl.w, the others after all big bricks
+        int po = a.r.p0 + excl.x, bi = excl.w, si = big_total + excl.y - excl.w, ni = excl.z;
+        if (excl.y + local.y > a.r.nbr || ni + local.z > a.r.nbr || bi + local.w > big_total ||
+            si + local.y - local.w > a.r.nbr) {  // tile sums out of step with the bricks
             atomicOr(&a.err[a.r.s0], MPM_EBIT_INTERNAL);
             pf = nf = 0u;
         }
@@ -153,12 +180,12 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(StepArgs a)
         for (int k = 0; k < kScanItems; ++k) {
             const int b = first + k;
             if (pf & (1u << k)) {
+                const int pi = (bf & (1u << k)) ? bi++ : si++;
                 sb.off[b] = po;
                 sb.act_brick[pi] = b;
                 sb.act_start[pi] = po;
                 sb.act_count[pi] = c[k];
                 sb.act_scene[pi] = s;
-                ++pi;
             }
             if (nf & (1u << k)) {
                 sb.nact_brick[ni] = b;

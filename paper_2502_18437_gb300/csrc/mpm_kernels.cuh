@@ -29,8 +29,9 @@ struct SortBufs {
     int* nact_scene;
     int* counters;  // [CTR_COUNT]
     int4* tile_sum; // [tiles] per scan tile (particles, active particle bricks, active node
-                    // bricks) of the next substep, added up by the key producers,
-                    // read by the scan and cleared by the scatter
+                    // bricks, particle bricks of at least kBigBrick particles) of the
+                    // next substep, added up by the key producers, read by the scan
+                    // and cleared by the scatter
     int tile_shift; // log2 of the bricks per scan tile
 };
 
@@ -73,6 +74,9 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 4;
 constexpr int kScanChunk = kScanThreads * kScanItems;  // bricks per pass of a scan CTA
 constexpr int kScatterPer = 4;  // particles per thread of the counting-sort scatter
+// Particle bricks of at least this many particles come first in the active list,
+// so the persistent transfer kernels end on small bricks (a shorter tail)
+constexpr int kBigBrick = 256;
 
 cudaError_t launch_prepare(const StepArgs& a, const PState& st, cudaStream_t s);
 cudaError_t launch_sort(const StepArgs& a, cudaStream_t s, bool write_perm = true);

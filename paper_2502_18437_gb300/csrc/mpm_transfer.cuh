@@ -111,6 +111,7 @@ __device__ __forceinline__ int aggregated_rank_mark(const SortBufs& sb, const Sc
             int4* ts = sb.tile_sum + sc.tile_base;
             base = atomicAdd(&sb.cnt[brick], np);
             if (add_x) atomicAdd(&ts[lb >> sb.tile_shift].x, np);
+            if (base < kBigBrick && base + np >= kBigBrick) atomicAdd(&ts[lb >> sb.tile_shift].w, 1);
             if (base == 0) {
                 atomicAdd(&ts[lb >> sb.tile_shift].y, 1);
                 const int nb = sc.nb;
