@@ -271,29 +271,116 @@ __device__ __forceinline__ void svd3(const float F[9], float U[9], float s[3], f
     s[2] = B[8];
 }
 
-// Left stretch of F for the constitutive update: the eigen-decomposition
-// F F^T = U diag(l) U^T (cyclic Jacobi, 4 sweeps, U accumulated) and the signed
-// singular values of the rotation-variant SVD F = U diag(s) V^T (V a rotation).
-// The two larger are sqrt(l); the smallest is det F / (their product), signed
-// like det F and accurate where sqrt of a tiny eigenvalue of F F^T is not.  V is
-// never formed: the stress needs U and s only, and the plastic return map is
-// F' = U diag(s'/s) U^T F.
-__device__ __forceinline__ void left_stretch(const float F[9], float U[9], float s[3])
+// Eigen-decomposition A = U diag(l) U^T of a symmetric 3x3 matrix in closed
+// form, after Eberly's robust 3x3 symmetric eigensolver: the characteristic
+// cubic of the deviator B = A - q I (q = tr A / 3) in its trigonometric form
+// (Smith 1961, the cosine solved here from the trisection cubic) gives the
+// eigenvalue farthest from the other two (the largest when det B >= 0, else
+// the smallest), whose eigenvector is the longest cross
+// product of two rows of A - l I; the 2x2 block of B in an orthonormal basis of
+// that vector's complement is then diagonalised by one exact Jacobi rotation.
+// Working on B keeps the rounding at the scale of the deviator's entries, and
+// the first eigenvalue is taken from its eigenvector (Rayleigh quotient).  The
+// columns of U are orthonormal to rounding (det U may be -1).  A deviator at
+// the rounding level of A (or a non-finite A) gives U = I and the diagonal.
+__device__ __forceinline__ void sym_eigen3(float a00, float a01, float a02, float a11, float a12, float a22,
+                                           float U[9], float l[3])
 {
-    float a00 = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
-    float a01 = F[0] * F[3] + F[1] * F[4] + F[2] * F[5];
-    float a02 = F[0] * F[6] + F[1] * F[7] + F[2] * F[8];
-    float a11 = F[3] * F[3] + F[4] * F[4] + F[5] * F[5];
-    float a12 = F[3] * F[6] + F[4] * F[7] + F[5] * F[8];
-    float a22 = F[6] * F[6] + F[7] * F[7] + F[8] * F[8];
+    const float q = (a00 + a11 + a22) * (1.0f / 3.0f);
+    const float b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
+    const float p2 = b00 * b00 + b11 * b11 + b22 * b22 + 2.0f * (a01 * a01 + a02 * a02 + a12 * a12);
 #pragma unroll
     for (int i = 0; i < 9; ++i) U[i] = (i % 4 == 0) ? 1.0f : 0.0f;
+    l[0] = a00;
+    l[1] = a11;
+    l[2] = a22;
+    if (!(p2 > 1e-13f * q * q)) return;
+    const float p = sqrtf(p2 * (1.0f / 6.0f));
+    const float ip = 1.0f / p;
+    const float c00 = b00 * ip, c11 = b11 * ip, c22 = b22 * ip, c01 = a01 * ip, c02 = a02 * ip, c12 = a12 * ip;
+    // det(B / p) / 2 = cos(3 phi); the eigenvalues are q + 2 p cos(phi + 2 pi k / 3).
+    // The one farthest from the others is q + 2 p c with c the largest root of the
+    // trisection cubic 4 c^3 - 3 c = |r| (in [cos(pi/6), 1]), signed like r (the
+    // cubic is odd): two Newton steps from the chord reach FP32 rounding.
+    const float det = c00 * (c11 * c22 - c12 * c12) - c01 * (c01 * c22 - c12 * c02) + c02 * (c01 * c12 - c11 * c02);
+    const float r = fminf(fmaxf(0.5f * det, -1.0f), 1.0f);
+    const float t = fabsf(r);
+    float c = 0.8660254f + 0.1339746f * t;
 #pragma unroll
-    for (int sweep = 0; sweep < 4; ++sweep) {
-        jacobi_rot(a00, a11, a01, a02, a12, U[0], U[1], U[3], U[4], U[6], U[7]);
-        jacobi_rot(a00, a22, a02, a01, a12, U[0], U[2], U[3], U[5], U[6], U[8]);
-        jacobi_rot(a11, a22, a12, a01, a02, U[1], U[2], U[4], U[5], U[7], U[8]);
+    for (int it = 0; it < 2; ++it) {
+        const float c2 = c * c;
+        c -= __fdividef(__fmaf_rn(4.0f, c2, -3.0f) * c - t, __fmaf_rn(12.0f, c2, -3.0f));
     }
+    const float d1 = copysignf(2.0f * p * c, r);  // l1 - q
+    const float m00 = b00 - d1, m11 = b11 - d1, m22 = b22 - d1;
+    // the longest cross product of two rows of A - l1 I
+    float e0 = a01 * a12 - a02 * m11, e1 = a02 * a01 - m00 * a12, e2 = m00 * m11 - a01 * a01;
+    float nn = e0 * e0 + e1 * e1 + e2 * e2;
+    {
+        const float x = a01 * m22 - a02 * a12, y = a02 * a02 - m00 * m22, z = m00 * a12 - a01 * a02;
+        const float n2 = x * x + y * y + z * z;
+        if (n2 > nn) { e0 = x; e1 = y; e2 = z; nn = n2; }
+    }
+    {
+        const float x = m11 * m22 - a12 * a12, y = a12 * a02 - a01 * m22, z = a01 * a12 - m11 * a02;
+        const float n2 = x * x + y * y + z * z;
+        if (n2 > nn) { e0 = x; e1 = y; e2 = z; nn = n2; }
+    }
+    if (!(nn > 0.0f)) return;
+    const float in = rsqrtf(nn);
+    const float v0 = e0 * in, v1 = e1 * in, v2 = e2 * in;
+    // orthonormal u, w with (v, u, w) a right-handed basis
+    float u0, u1, u2;
+    if (fabsf(v0) > fabsf(v1)) {
+        const float k = rsqrtf(v0 * v0 + v2 * v2);
+        u0 = -v2 * k; u1 = 0.0f; u2 = v0 * k;
+    } else {
+        const float k = rsqrtf(v1 * v1 + v2 * v2);
+        u0 = 0.0f; u1 = v2 * k; u2 = -v1 * k;
+    }
+    const float w0 = v1 * u2 - v2 * u1, w1 = v2 * u0 - v0 * u2, w2 = v0 * u1 - v1 * u0;
+    // B v, B u, B w
+    const float bv0 = b00 * v0 + a01 * v1 + a02 * v2, bv1 = a01 * v0 + b11 * v1 + a12 * v2,
+                bv2 = a02 * v0 + a12 * v1 + b22 * v2;
+    const float bu0 = b00 * u0 + a01 * u1 + a02 * u2, bu1 = a01 * u0 + b11 * u1 + a12 * u2,
+                bu2 = a02 * u0 + a12 * u1 + b22 * u2;
+    const float bw0 = b00 * w0 + a01 * w1 + a02 * w2, bw1 = a01 * w0 + b11 * w1 + a12 * w2,
+                bw2 = a02 * w0 + a12 * w1 + b22 * w2;
+    const float muu = u0 * bu0 + u1 * bu1 + u2 * bu2, muw = w0 * bu0 + w1 * bu1 + w2 * bu2,
+                mww = w0 * bw0 + w1 * bw1 + w2 * bw2;
+    l[0] = q + (v0 * bv0 + v1 * bv1 + v2 * bv2);
+    // the 2x2 block [[muu, muw], [muw, mww]]: one rotation (textbook tangent of
+    // the smaller angle, as in jacobi_rot)
+    float cr = 1.0f, sr = 0.0f, tm = 0.0f;
+    if (fabsf(muw) > 2.98e-8f * fmaxf(fabsf(muu + q), fabsf(mww + q))) {
+        const float d = mww - muu, b = 2.0f * muw;
+        const float den = fmaxf(fabsf(d) + approx_sqrt(__fmaf_rn(d, d, b * b)), fabsf(b));
+        const float t = __fdividef(d >= 0.0f ? b : -b, den);
+        cr = rsqrtf(__fmaf_rn(t, t, 1.0f));
+        sr = t * cr;
+        tm = t * muw;
+    }
+    l[1] = q + (muu - tm);
+    l[2] = q + (mww + tm);
+    U[0] = v0; U[3] = v1; U[6] = v2;
+    U[1] = cr * u0 - sr * w0; U[4] = cr * u1 - sr * w1; U[7] = cr * u2 - sr * w2;
+    U[2] = sr * u0 + cr * w0; U[5] = sr * u1 + cr * w1; U[8] = sr * u2 + cr * w2;
+}
+
+// Left stretch of F for the constitutive update: the eigen-decomposition
+// F F^T = U diag(l) U^T (closed form, sym_eigen3) and the signed singular
+// values of the rotation-variant SVD F = U diag(s) V^T.  The two larger are
+// sqrt(l); the smallest is det F / (their product), signed like det F and
+// accurate where sqrt of a tiny eigenvalue of F F^T is not.  V is never formed:
+// the stress needs U and s only, and the plastic return map is
+// F' = U diag(s'/s) U^T F; neither depends on the signs of U's columns.
+__device__ __forceinline__ void left_stretch(const float F[9], float U[9], float s[3])
+{
+    float l[3];
+    sym_eigen3(F[0] * F[0] + F[1] * F[1] + F[2] * F[2], F[0] * F[3] + F[1] * F[4] + F[2] * F[5],
+               F[0] * F[6] + F[1] * F[7] + F[2] * F[8], F[3] * F[3] + F[4] * F[4] + F[5] * F[5],
+               F[3] * F[6] + F[4] * F[7] + F[5] * F[8], F[6] * F[6] + F[7] * F[7] + F[8] * F[8], U, l);
+    const float a00 = l[0], a11 = l[1], a22 = l[2];
     const float J = det3(F);
     const float r0 = approx_sqrt(a00), r1 = approx_sqrt(a11), r2 = approx_sqrt(a22);
     // smallest eigenvalue: its singular value from the determinant
