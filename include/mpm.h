@@ -109,8 +109,10 @@ enum {
                                    576 or 768 (default)                             */
     MPM_OPT_FUSED = 9,          /* 1: fuse each substep's G2P with the next substep's
                                    P2G; 0 (default): separate P2G and G2P kernels */
-    MPM_OPT_G2P_REGS64 = 10     /* 1 (default): G2P variant limited to 64 registers
-                                   (more resident warps); 0: up to 80 registers     */
+    MPM_OPT_G2P_REGS64 = 10     /* 1: G2P variant limited to 64 registers (more
+                                   resident warps); 0 (default): the larger budget
+                                   (72 registers at 128 threads, 80 at 256, 112
+                                   at 512)                                          */
 };
 
 /* ---- configuration --------------------------------------------------- */

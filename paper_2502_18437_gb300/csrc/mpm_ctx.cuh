@@ -59,7 +59,7 @@ struct mpm_ctx {
     int launch_mode = 0;
     int p2g_chunk = 4 * mpm::kP2GThreads;
     int g2p_threads = 128;
-    int g2p_regs64 = 1;
+    int g2p_regs64 = 0;
     int ctas_per_sm = 0;
     int graph_chunk = 32;
     int phase_timing = 0;

@@ -1721,15 +1721,15 @@ static void launch_g2p_variant(const StepArgs& a, cudaStream_t s)
         }
     } else {
         switch (a.g2p_threads) {
-        case 128: k_g2p<128, 6, FLAGS><<<c, 128, 0, s>>>(a); break;
+        case 128: k_g2p<128, 7, FLAGS><<<c, 128, 0, s>>>(a); break;
         case 512: k_g2p<512, 1, FLAGS><<<c, 512, 0, s>>>(a); break;
         default: k_g2p<256, 3, FLAGS><<<c, 256, 0, s>>>(a); break;
         }
     }
 }
 
-// The standard-MPM and PB-MPM variants exist in the default launch shape only
-// (128 threads, 64 registers): the MLS-MPM shapes are what the tuner explores.
+// The standard-MPM and PB-MPM variants exist in one launch shape only (128
+// threads, 64 registers): the MLS-MPM shapes are what the tuner explores.
 cudaError_t launch_g2p(const StepArgs& a, cudaStream_t s)
 {
     const int c = a.persistent_ctas;
@@ -1828,7 +1828,7 @@ int occupancy_g2p(int threads, int regs64)
         else if (threads == 512) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<512, 2, kG2PSolids>, 512, 0);
         else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<256, 4, kG2PSolids>, 256, 0);
     } else {
-        if (threads == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<128, 6, kG2PSolids>, 128, 0);
+        if (threads == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<128, 7, kG2PSolids>, 128, 0);
         else if (threads == 512) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<512, 1, kG2PSolids>, 512, 0);
         else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_g2p<256, 3, kG2PSolids>, 256, 0);
     }
