@@ -98,8 +98,10 @@ enum {
                                    1: one launch per phase per scene (looped)       */
     MPM_OPT_P2G_THREADS = 3,    /* threads per CTA of the P2G kernel: fixed at 192
                                    (64 cells x 3 node slices); other values rejected */
-    MPM_OPT_G2P_THREADS = 4,    /* threads per CTA of the G2P kernel: 128 (default) /
-                                   256 / 512                                        */
+    MPM_OPT_G2P_THREADS = 4,    /* threads per CTA of the G2P kernel: 128 / 256 / 512,
+                                   or 0 (default): 256 for launches of fewer than
+                                   524,288 particles, else 128 (reads back the shape
+                                   of a launch over all scenes)                      */
     MPM_OPT_CTAS_PER_SM = 5,    /* persistent CTAs per SM for P2G/G2P (0 = occupancy max) */
     MPM_OPT_GRAPH_CHUNK = 6,    /* most substeps captured per graph (1..64, default 32):
                                    a call of k substeps replays ceil(k/chunk) graphs */

@@ -116,6 +116,17 @@ void clear_graphs(mpm_ctx* c)
     c->graphs.clear();
 }
 
+// G2P CTA size of a launch over np particles: the set value, or by default 256
+// threads below 512k particles (fewer particle bricks than 128-thread CTA slots:
+// more threads per brick shorten each CTA's brick) and 128 above.  The
+// standard-MPM and PB-MPM G2P variants exist at 128 threads only.
+static int g2p_threads_for(const mpm_ctx* c, int np)
+{
+    if (c->cfg.solver != MPM_SOLVER_MLS) return 128;
+    if (c->g2p_threads) return c->g2p_threads;
+    return np < (1 << 19) ? 256 : 128;
+}
+
 static int cap_occ(const mpm_ctx* c, int occ)
 {
     if (occ < 1) occ = 1;
@@ -156,9 +167,10 @@ StepArgs step_args(mpm_ctx* c, float dt, int s0, int s1, const PState& in, const
     a.plasticity = c->cfg.plasticity;
     a.yield_stress = c->cfg.yield_stress;
     // the occupancy queries are host calls: ask once per variant and context
-    const int ti = c->g2p_threads == 128 ? 0 : c->g2p_threads == 512 ? 2 : 1;
+    const int g2p_threads = g2p_threads_for(c, a.r.np);
+    const int ti = g2p_threads == 128 ? 0 : g2p_threads == 512 ? 2 : 1;
     int& og = c->occ_g2p[c->g2p_regs64 ? 1 : 0][ti];
-    if (!og) og = std::max(1, occupancy_g2p(c->g2p_threads, c->g2p_regs64));
+    if (!og) og = std::max(1, occupancy_g2p(g2p_threads, c->g2p_regs64));
     int& op = c->occ_p2g[c->p2g_chunk / kP2GThreads - 2];
     if (!op) op = std::max(1, occupancy_p2g(c->p2g_chunk));
     if (!c->occ_grid) c->occ_grid = std::max(1, occupancy_grid());
@@ -171,7 +183,7 @@ StepArgs step_args(mpm_ctx* c, float dt, int s0, int s1, const PState& in, const
     a.grid_plain_ctas = c->num_sms * c->occ_grid_plain;
     a.fused_ctas = c->num_sms * cap_occ(c, c->occ_fused);
     a.p2g_chunk = c->p2g_chunk;
-    a.g2p_threads = c->g2p_threads;
+    a.g2p_threads = g2p_threads;
     a.cell_order = 1;
     a.solver = c->cfg.solver;
     a.pb_beta = c->cfg.pb_beta;
@@ -476,7 +488,7 @@ extern "C" int mpm_get_option(mpm_ctx* c, int option, int64_t* value)
     case MPM_OPT_USE_GRAPHS: *value = c->use_graphs; break;
     case MPM_OPT_LAUNCH_MODE: *value = c->launch_mode; break;
     case MPM_OPT_P2G_THREADS: *value = kP2GThreads; break;
-    case MPM_OPT_G2P_THREADS: *value = c->g2p_threads; break;
+    case MPM_OPT_G2P_THREADS: *value = g2p_threads_for(c, c->total_particles); break;
     case MPM_OPT_CTAS_PER_SM: *value = c->ctas_per_sm; break;
     case MPM_OPT_GRAPH_CHUNK: *value = c->graph_chunk; break;
     case MPM_OPT_PHASE_TIMING: *value = c->phase_timing; break;
@@ -506,7 +518,7 @@ extern "C" int mpm_set_option(mpm_ctx* c, int option, int64_t value)
         c->p2g_chunk = (int)value;
         break;
     case MPM_OPT_G2P_THREADS:
-        if (value != 128 && value != 256 && value != 512) return MPM_ERR_INVALID_ARGUMENT;
+        if (value != 0 && value != 128 && value != 256 && value != 512) return MPM_ERR_INVALID_ARGUMENT;
         c->g2p_threads = (int)value;
         break;
     case MPM_OPT_CTAS_PER_SM:

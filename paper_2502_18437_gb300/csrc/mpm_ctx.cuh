@@ -58,7 +58,7 @@ struct mpm_ctx {
     int use_graphs = 1;
     int launch_mode = 0;
     int p2g_chunk = 4 * mpm::kP2GThreads;
-    int g2p_threads = 128;
+    int g2p_threads = 0;  // 0: by the launch's particle count
     int g2p_regs64 = 0;
     int ctas_per_sm = 0;
     int graph_chunk = 32;
