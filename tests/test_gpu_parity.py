@@ -224,6 +224,41 @@ def test_degenerate_F_fixed_corotated():
     check_fields(sc, out, st, Scales(sc, F))
 
 
+def _rotation(g):
+    q, r = np.linalg.qr(g.normal(size=(3, 3)))
+    q = q * np.sign(np.diag(r))
+    return q if np.linalg.det(q) > 0 else -q
+
+
+@pytest.mark.parametrize("model", ["fixed_corotated", "neo_hookean"])
+@pytest.mark.parametrize("plastic", [False, True])
+def test_stress_exact_eigen_structures_matches_oracle(model, plastic):
+    # F = R diag(s) Q^T with exactly repeated, symmetric and separated singular
+    # values: the left stretch's eigenvalues are double (larger or smaller pair),
+    # triple (isotropic, a scaled rotation), evenly spaced around their mean, or
+    # generic, and one case is a pure rotation.  The closed-form eigen-decomposition
+    # meets its special cases here (deviator zero, the cubic's cosine at +-1 and 0);
+    # every field equals the oracle's one substep, with and without the von Mises
+    # return map (yield low enough that the larger strains yield).
+    sc = W.elastic_cube(model=model, n_side=10)
+    if plastic:
+        sc = dict(sc, plasticity=True, yield_stress=20.0)
+    N = len(sc["x"])
+    g = np.random.default_rng(31)
+    sv = [(1.2, 1.2, 0.8), (1.2, 0.8, 0.8), (0.9, 0.9, 0.9), (0.9, 1.0, 1.1), (1.5, 1.0, 0.6),
+          (1.0, 1.0, 1.0), (1.0, 1.0 + 1e-4, 1.0 + 1e-4)]
+    if model == "fixed_corotated" and not plastic:
+        sv.append((1.1, 0.9, -0.7))  # inverted
+    F = np.stack([_rotation(g) @ np.diag(sv[i % len(sv)]) @ _rotation(g).T for i in range(N)]).astype(np.float32)
+    C = np.zeros((N, 3, 3), np.float32)
+    x, v, C, F, out = gpu_one_step(sc, sc["v"], C, F)
+    st, gm, gv, err, _ = oracle_one_step(sc, x, v, C, F)
+    assert err == 0
+    for f in ("x", "v", "C", "F"):
+        assert np.all(np.isfinite(out[f])), f
+    check_fields(sc, out, st, Scales(sc, F))
+
+
 @pytest.mark.parametrize("steps_before", [0, 15])
 def test_box_contact_matches_oracle(steps_before):
     # A rotated box (Sec. IV-A, solid SDF, Eq. 11 friction) pressed down into a
