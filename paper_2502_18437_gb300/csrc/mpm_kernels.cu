@@ -311,6 +311,11 @@ __global__ void __launch_bounds__(256) k_prepare(StepArgs a, PState st)
 // At the end of the pass the window is added to HBM with one vector reduction
 // per node.  Stage and windows reuse the record slots.
 
+__device__ __forceinline__ void prefetch_l2(const float* p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 constexpr int kP2GSlotPitch = 33;  // 32 lanes + 1: rows of one item fall in different banks
 // record slots of a pass of PER x 192 particles (the rows of the interleaved
 // layout; 768-particle passes need 24).  A smaller record area leaves more of
@@ -392,6 +397,27 @@ __global__ void __launch_bounds__(kP2GThreads, 4) k_p2g(StepArgs a)
                         pc[u] = (l0 * 4 + l1) * 4 + l2;
                     }
                     pr[u] = atomicAdd(&cell_cnt[pc[u]], 1);
+                }
+            }
+            // the pass's particle fields start towards L2 while warp 0 builds the items
+            // (phase A2 then loads them from L2 rather than from HBM)
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                if (pc[u] < 0) continue;
+                const int p = pp[u];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    prefetch_l2(a.in.x + (size_t)q * cap + p);
+                    prefetch_l2(a.in.v + (size_t)q * cap + p);
+                }
+#pragma unroll
+                for (int q = 0; q < 9; ++q) prefetch_l2(a.in.C + (size_t)q * cap + p);
+                if (MODE == kP2GStress && a.tau_valid) {
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) prefetch_l2(a.in.tau + (size_t)q * cap + p);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) prefetch_l2(a.in.F + (size_t)q * cap + p);
                 }
             }
             __syncthreads();
