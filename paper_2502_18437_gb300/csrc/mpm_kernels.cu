@@ -1065,7 +1065,8 @@ enum {
 template <int FLAGS>
 __device__ __forceinline__ unsigned g2p_particle(const StepArgs& a, const SceneDev& sc, const float4* lin, int p, int s,
                                                  int ox, int oy, int oz, G2POut& o, float* sX = nullptr,
-                                                 float* sF = nullptr, int stride = 0, int pnext = -1)
+                                                 float* sF = nullptr, int stride = 0, int pnext = -1,
+                                                 int* sI = nullptr)
 {
     const int cap = a.cap, n = sc.n;
     const float fn = (float)n, dt = a.dt;
@@ -1073,6 +1074,7 @@ __device__ __forceinline__ unsigned g2p_particle(const StepArgs& a, const SceneD
     if (sX) cp_async_wait_all();
     const float x0 = sX ? sX[0] : a.in.x[p], x1 = sX ? sX[stride] : a.in.x[cap + p],
                 x2 = sX ? sX[2 * stride] : a.in.x[2 * cap + p];
+    const int id_staged = sI ? sI[0] : 0;  // read before the next particle's copy lands
     int bc[3];
     float f[3], w[9];
     particle_weights(x0, x1, x2, n, bc, f, w);
@@ -1128,6 +1130,7 @@ __device__ __forceinline__ unsigned g2p_particle(const StepArgs& a, const SceneD
     if (sX && pnext >= 0) {
 #pragma unroll
         for (int d = 0; d < 3; ++d) cp_async4(sX + d * stride, a.in.x + (size_t)d * cap + pnext);
+        if (sI) cp_async4(reinterpret_cast<float*>(sI), reinterpret_cast<const float*>(a.in.id + pnext));
     }
     // C = D^-1 sum N v (x_I - x_p)^T = 4/dx^2 * dx * B  (Eq. 9), or for the
     // standard MPM L = n B with the derivative weights (Eq. 5); x += dt v (Eq. 4)
@@ -1142,7 +1145,7 @@ __device__ __forceinline__ unsigned g2p_particle(const StepArgs& a, const SceneD
     for (int d = 0; d < 3; ++d) a.out.v[(size_t)d * cap + s] = o.v[d];
 #pragma unroll
     for (int i = 0; i < 9; ++i) a.out.C[(size_t)i * cap + s] = o.C[i];
-    a.out.id[s] = a.in.id[p];
+    a.out.id[s] = sI ? id_staged : a.in.id[p];
     float mu, lam;
     if (sc.pp_mat) {
         mu = a.in.mu[p];
@@ -1209,8 +1212,11 @@ template <int BLOCK, int MINB, int FLAGS>
 __global__ void __launch_bounds__(BLOCK, MINB) k_g2p(StepArgs a)
 {
     constexpr bool SOLIDS = (FLAGS & kG2PSolids) != 0;
-    // x and F of each thread's next particle, copied by cp.async one particle ahead
+    // x, F and (with 72 or more registers; the 64-register builds would spill) the
+    // id of each thread's next particle, copied by cp.async one particle ahead
+    constexpr bool STAGE_ID = 65536 / (BLOCK * MINB) >= 72;
     __shared__ float sX[3 * BLOCK], sF[9 * BLOCK];
+    __shared__ int sI[STAGE_ID ? BLOCK : 1];
     __shared__ __align__(128) float4 vw[2][8 * 64];
     __shared__ __align__(16) float4 lin[kWinNodes];
     __shared__ __align__(8) unsigned long long bar[2];
@@ -1246,6 +1252,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_g2p(StepArgs a)
             for (int d = 0; d < 3; ++d) cp_async4(&sX[d * BLOCK + tid], a.in.x + (size_t)d * a.cap + pcur);
 #pragma unroll
             for (int q = 0; q < 9; ++q) cp_async4(&sF[q * BLOCK + tid], a.in.F + (size_t)q * a.cap + pcur);
+            if (STAGE_ID) cp_async4(reinterpret_cast<float*>(&sI[tid]), reinterpret_cast<const float*>(a.in.id + pcur));
         }
         linearize_window<BLOCK>(vw[buf], lin);
         __syncthreads();
@@ -1259,7 +1266,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_g2p(StepArgs a)
                 G2POut o;
                 const int pnext = k + BLOCK < count ? a.sb.perm[start + k + BLOCK] : -1;
                 ebits |= g2p_particle<FLAGS>(a, sc, lin, pcur, start + k, ox, oy, oz, o, &sX[tid], &sF[tid], BLOCK,
-                                             pnext);
+                                             pnext, STAGE_ID ? &sI[tid] : nullptr);
                 pcur = pnext;
                 if (!(FLAGS & kG2PNoStress))
 #pragma unroll
