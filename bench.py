@@ -218,21 +218,43 @@ def kernel_source_digest():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel):
-    """DRAM bytes (read + write) per launch of `kernel` from its ncu summary under
-    profiles/, or None when the summary is missing or the sources changed since."""
+def recorded_profile(kernel):
+    """Per-launch figures of `kernel`'s ncu summary under profiles/ (DRAM traffic,
+    warp instructions), or {} when the summary is missing or the CUDA sources
+    changed since the capture."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_tissue_block_1m.md")
     if not os.path.exists(path):
-        return None
+        return {}
     fields = {}
+    keys = ("traffic_bytes_per_launch", "warp_instructions_per_launch", "source_digest")
     with open(path) as fh:
         for line in fh:
-            if ":" in line and line.split(":", 1)[0] in ("traffic_bytes_per_launch", "source_digest"):
+            if ":" in line and line.split(":", 1)[0] in keys:
                 k, v = line.split(":", 1)
                 fields[k] = v.strip()
-    if fields.get("source_digest") != kernel_source_digest() or "traffic_bytes_per_launch" not in fields:
+    if fields.pop("source_digest", None) != kernel_source_digest():
+        return {}
+    return {k: int(v) for k, v in fields.items()}
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes (read + write) per launch of `kernel` from its ncu summary, or None."""
+    return recorded_profile(kernel).get("traffic_bytes_per_launch")
+
+
+def issue_roofline(kernel, launch_ms, sm_count, sm_mhz):
+    """Instruction-issue roofline of `kernel`: its warp instructions per launch
+    (ncu, impact phase) over its launch duration, against one warp instruction
+    per cycle on each of the 4 schedulers of every SM at the sampled SM clock;
+    None without a current ncu summary."""
+    instr = recorded_profile(kernel).get("warp_instructions_per_launch")
+    if not instr or not launch_ms or not sm_count or not sm_mhz:
         return None
-    return int(fields["traffic_bytes_per_launch"])
+    peak = sm_count * 4 * sm_mhz * 1e6 / 1e9  # G warp instructions / s
+    achieved = instr / (launch_ms / 1e3) / 1e9
+    return {"kernel": kernel, "warp_instructions": instr, "achieved": round(achieved, 1), "peak": round(peak, 1),
+            "unit": "G warp instructions/s", "frac": round(achieved / peak, 4),
+            "floor_ms": round(instr / (peak * 1e9) * 1e3, 5), "launch_ms": round(launch_ms, 5)}
 
 
 def roofline_fields(N, bricks, active_nodes, per_launch_ms, substep_ms, peak, peak_kind, pp_mat=False):
@@ -389,6 +411,13 @@ def run_ours(args):
         for name, w in win.items()}
     roofline["timing"] = ("per-phase CUDA events on the context's stream over the whole 500-substep "
                           "trajectory (direct launches); the headline value is graph replay")
+    # the kernels move their algorithmic bytes at a fraction of the HBM peak; the issue
+    # rate of their instructions (ncu counts of the impact-phase launch against the
+    # impact window's mean launch duration) is the bound beside it
+    props = torch.cuda.get_device_properties(local)
+    roofline["issue"] = {k: issue_roofline(k, win["impact"]["ms"][names.index(k)] / win["impact"]["substeps"],
+                                           props.multi_processor_count, clk.get("sm_mhz"))
+                         for k in ("g2p", "p2g")}
 
     chunk = sim.get_option("graph_chunk")
     graphs = -(-SUBSTEPS_PER_STEP // chunk)

@@ -30,6 +30,23 @@ def test_recorded_traffic_follows_the_digest(tmp_path, monkeypatch):
     assert bench.recorded_traffic("g2p") is None
 
 
+def test_issue_roofline_from_the_recorded_instructions(tmp_path, monkeypatch):
+    digest = bench.kernel_source_digest()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_digest", lambda: digest)
+    assert bench.issue_roofline("g2p", 0.07, 152, 2070.0) is None  # no summary
+    d = tmp_path / "profiles"
+    d.mkdir()
+    (d / "g2p_tissue_block_1m.md").write_text(
+        f"traffic_bytes_per_launch: 1\nwarp_instructions_per_launch: 46000000\nsource_digest: {digest}\n")
+    r = bench.issue_roofline("g2p", 0.0736, 152, 2070.0)
+    peak = 152 * 4 * 2.070  # G warp instructions per second
+    assert r["peak"] == round(peak, 1)
+    assert abs(r["frac"] - 46e6 / 0.0736e-3 / 1e9 / peak) < 1e-4
+    assert abs(r["floor_ms"] - 46e6 / (peak * 1e9) * 1e3) < 1e-5
+    assert bench.issue_roofline("g2p", 0.0736, 152, None) is None  # no clock sample
+
+
 def test_source_digest_changes_with_any_kernel_source(tmp_path, monkeypatch):
     csrc = tmp_path / "paper_2502_18437_gb300" / "csrc"
     csrc.mkdir(parents=True)
