@@ -101,6 +101,18 @@ static bool is_pinned_host(const void* p)
     return at.type == cudaMemoryTypeHost;
 }
 
+// Device address of page-locked, mapped host memory (kernels read or write it
+// directly over the host link), or null for any other pointer.
+static void* mapped_host(const void* p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 int upload_scenes(mpm_ctx* c)
 {
     if (!c->scenes_dirty) return MPM_OK;
@@ -828,6 +840,27 @@ extern "C" int mpm_read_state(mpm_ctx* c, int scene, uint32_t fields, void* cons
             ++nf;
         }
     int st;
+    const PState cur = c->st[c->cur];
+    if (mem == MPM_MEM_HOST && !(fields & ~15u) && np > 0) {
+        // pinned host arrays: one kernel writes them in id order over the host link
+        HostFields h{};
+        bool mapped = true;
+        for (int f = 0, k = 0; f < 4; ++f)
+            if (fields & (1u << f)) {
+                h.f[f] = static_cast<float*>(mapped_host(dst[k++]));
+                mapped = mapped && h.f[f];
+            }
+        if (mapped) {
+            if ((st = ensure_stage(c, sizeof(int) * (size_t)np))) return st;
+            if ((st = ensure_pinned(c, 64))) return st;
+            int* inv = static_cast<int*>(c->d_stage);
+            MPM_CK(launch_id_inverse(cur, sc.p_begin, np, inv, c->stream));
+            MPM_CK(launch_fields_host(cur, c->cap, sc.p_begin, np, inv, h, true, c->stream));
+            MPM_CK(cudaMemcpyAsync(c->h_pinned, c->d_err + scene, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+            if ((st = wait_stream(c))) return st;
+            return error_status(*static_cast<unsigned*>(c->h_pinned));
+        }
+    }
     // device staging for host reads that are not pinned
     size_t stage_need = 0, pin_need = 64;
     for (int f = 0, k = 0; f < 6; ++f) {
@@ -844,7 +877,6 @@ extern "C" int mpm_read_state(mpm_ctx* c, int scene, uint32_t fields, void* cons
     size_t soff = 0, poff = 64;
     struct Pending { void* dst; size_t poff, bytes; };
     std::vector<Pending> pend;
-    const PState cur = c->st[c->cur];
     for (int f = 0, k = 0; f < 6; ++f) {
         if (!(fields & (1u << f))) continue;
         void* out = dst[k++];
@@ -892,9 +924,28 @@ extern "C" int mpm_write_state(mpm_ctx* c, int scene, uint32_t fields, const voi
             need += align256(sizeof(float) * kFieldComps[f] * (size_t)np);
         }
     int st = MPM_OK;
+    const PState cur = c->st[c->cur];
+    if (mem == MPM_MEM_HOST && np > 0) {
+        // pinned host arrays: one kernel reads them in id order over the host link
+        HostFields h{};
+        bool mapped = true;
+        for (int f = 0, k = 0; f < 4; ++f)
+            if (fields & (1u << f)) {
+                h.f[f] = static_cast<float*>(mapped_host(src[k++]));
+                mapped = mapped && h.f[f];
+            }
+        if (mapped) {
+            if ((st = ensure_stage(c, sizeof(int) * (size_t)np))) return st;
+            int* inv = static_cast<int*>(c->d_stage);
+            MPM_CK(launch_id_inverse(cur, sc.p_begin, np, inv, c->stream));
+            MPM_CK(launch_fields_host(cur, c->cap, sc.p_begin, np, inv, h, false, c->stream));
+            if (fields & MPM_FIELD_X) c->keys_valid = false;
+            invalidate_pending(c);
+            return wait_stream(c);
+        }
+    }
     if (mem == MPM_MEM_HOST && (st = ensure_stage(c, need))) return st;
     size_t off = 0;
-    const PState cur = c->st[c->cur];
     for (int f = 0, k = 0; f < 4; ++f) {
         if (!(fields & (1u << f))) continue;
         const size_t bytes = sizeof(float) * kFieldComps[f] * (size_t)np;

@@ -11,6 +11,7 @@
 //              domain walls, reset of the P2G accumulator
 //   k_g2p      G2P (Eq. 4, Eq. 9, Eq. 10) with the 2x2x2-brick velocity halo
 //              staged by bulk-copy TMA, plasticity, next brick key + rank
+#include <cstdint>
 #include <cstdio>
 
 #include "mpm_transfer.cuh"
@@ -1624,6 +1625,67 @@ __global__ void k_scatter_field(PState st, int cap, int p0, int np, int field, c
     for (int c = 0; c < comps; ++c) dst[(size_t)c * cap + s] = in[c];
 }
 
+// Inverse of a scene's slot -> id map: inv[id] = slot.
+__global__ void k_id_inverse(PState st, int p0, int np, int* inv)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= np) return;
+    const int id = st.id[p0 + g];
+    if ((unsigned)id < (unsigned)np) inv[id] = p0 + g;
+}
+
+// State fields <-> host-mapped arrays (pinned host memory the kernel reads or
+// writes directly over the host link), in particle-id order: a CTA takes the
+// kIoBlock consecutive ids of one contiguous chunk of each host array, so the
+// host side moves as whole 16-byte words; the slot side (device memory) is the
+// scattered one.  Fields pass one at a time through shared memory.
+constexpr int kIoBlock = 128;
+
+template <bool TO_HOST>
+__global__ void __launch_bounds__(kIoBlock) k_fields_host(PState st, int cap, int p0, int np,
+                                                          const int* __restrict__ inv, HostFields h)
+{
+    __shared__ __align__(16) float buf[9 * kIoBlock];
+    const int t = threadIdx.x;
+    const int g0 = blockIdx.x * kIoBlock;
+    const int cnt = min(kIoBlock, np - g0);
+    // the slot of id g0 + t (ids are a permutation of the scene's slots)
+    const int s = t < cnt ? inv[g0 + t] : p0;
+    const bool own = t < cnt && (unsigned)(s - p0) < (unsigned)np;
+#pragma unroll 1
+    for (int f = 0; f < 4; ++f) {
+        float* hp = h.f[f];
+        if (!hp) continue;
+        const int k = f < 2 ? 3 : 9;
+        float* soa = f == 0 ? st.x : f == 1 ? st.v : f == 2 ? st.C : st.F;
+        float* chunk = hp + (size_t)g0 * k;
+        const int nflt = cnt * k;
+        const bool vec = cnt == kIoBlock && (reinterpret_cast<uintptr_t>(chunk) & 15u) == 0;
+        if (TO_HOST) {
+            if (own)
+                for (int c = 0; c < k; ++c) buf[t * k + c] = soa[(size_t)c * cap + s];
+            __syncthreads();
+            if (vec) {
+                for (int i = t; i < nflt / 4; i += kIoBlock)
+                    reinterpret_cast<float4*>(chunk)[i] = reinterpret_cast<const float4*>(buf)[i];
+            } else {
+                for (int i = t; i < nflt; i += kIoBlock) chunk[i] = buf[i];
+            }
+        } else {
+            if (vec) {
+                for (int i = t; i < nflt / 4; i += kIoBlock)
+                    reinterpret_cast<float4*>(buf)[i] = reinterpret_cast<const float4*>(chunk)[i];
+            } else {
+                for (int i = t; i < nflt; i += kIoBlock) buf[i] = chunk[i];
+            }
+            __syncthreads();
+            if (own)
+                for (int c = 0; c < k; ++c) soa[(size_t)c * cap + s] = buf[t * k + c];
+        }
+        __syncthreads();  // buf is the next field's
+    }
+}
+
 __global__ void k_init_particles(PState st, int cap, int p_at, int n, int id0, const float* x, const float* v,
                                  const float* E, const float* nu, float E0, float nu0)
 {
@@ -1813,6 +1875,22 @@ cudaError_t launch_gather_field(const PState& st, int cap, int p0, int np, int f
 {
     if (np == 0) return cudaSuccess;
     k_gather_field<<<n_blocks(np, 256), 256, 0, s>>>(st, cap, p0, np, field, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_id_inverse(const PState& st, int p0, int np, int* inv, cudaStream_t s)
+{
+    if (np == 0) return cudaSuccess;
+    k_id_inverse<<<n_blocks(np, 256), 256, 0, s>>>(st, p0, np, inv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fields_host(const PState& st, int cap, int p0, int np, const int* inv, const HostFields& h,
+                               bool to_host, cudaStream_t s)
+{
+    if (np == 0) return cudaSuccess;
+    if (to_host) k_fields_host<true><<<n_blocks(np, kIoBlock), kIoBlock, 0, s>>>(st, cap, p0, np, inv, h);
+    else k_fields_host<false><<<n_blocks(np, kIoBlock), kIoBlock, 0, s>>>(st, cap, p0, np, inv, h);
     return cudaGetLastError();
 }
 

@@ -102,6 +102,15 @@ cudaError_t launch_permute_to_id(const PState& src, const PState& dst, int cap, 
                                  cudaStream_t s);
 cudaError_t launch_scatter_field(const PState& st, int cap, int p0, int np, int field, const float* src,
                                  cudaStream_t s);
+// x, v, C, F (null: not moved) of one scene as host-mapped arrays in particle-id order
+struct HostFields {
+    float* f[4];
+};
+// inv[id] = slot of the scene's particle with that id (np entries)
+cudaError_t launch_id_inverse(const PState& st, int p0, int np, int* inv, cudaStream_t s);
+// state fields <-> host-mapped arrays in one pass (to_host: state -> host)
+cudaError_t launch_fields_host(const PState& st, int cap, int p0, int np, const int* inv, const HostFields& h,
+                               bool to_host, cudaStream_t s);
 cudaError_t launch_read_grid(const float4* V, const int* brick_epoch, const int* epoch, const SceneDev* scenes,
                              int scene, int n, int brick_base, float* dst, cudaStream_t s);
 int occupancy_p2g(int chunk);

@@ -117,6 +117,60 @@ def test_device_tensors_roundtrip():
         assert np.array_equal(sim.read_state(0, ("v",))["v"], 2 * host["v"])
 
 
+@pytest.mark.parametrize("misalign", [False, True])
+def test_pinned_host_state_io_matches_staged_path(misalign):
+    # Pinned host arrays take the one-kernel path over the host link (state <->
+    # id-ordered arrays through the id inverse); pageable ones the staged path.
+    # Two scenes (the second starts at a nonzero slot), counts that are not
+    # multiples of the kernel's 128-id blocks, storage permuted by the sort; with
+    # misalign the arrays start 4 bytes into their allocation (no 16-byte words).
+    torch = pytest.importorskip("torch")
+    scenes = [W.elastic_cube(n_side=7), W.elastic_cube(n_side=9, corner=(0.3, 0.12, 0.3))]
+    g = np.random.default_rng(5)
+    shapes = {"x": (3,), "v": (3,), "C": (3, 3), "F": (3, 3)}
+    masks = {"x": mpm.FIELD["x"], "v": mpm.FIELD["v"], "C": mpm.FIELD["C"], "F": mpm.FIELD["F"]}
+
+    def pinned(n, shape):
+        k = int(np.prod(shape))
+        t = torch.empty(n * k + (1 if misalign else 0), dtype=torch.float32).pin_memory()
+        a = t.numpy()[(1 if misalign else 0):].reshape((n,) + shape)
+        return t, a
+
+    with mpm.from_scenes(scenes) as sim:
+        sim.substep(1e-4, 4)
+        for scene, sc in enumerate(scenes):
+            N = len(sc["x"])
+            ref = sim.read_state(scene)  # pageable: staged path
+            keep, arrs = [], {}
+            for f, sh in shapes.items():
+                t, a = pinned(N, sh)
+                keep.append(t)
+                arrs[f] = a
+            st = mpm.mpm_read_state(sim.h, scene, 15, [arrs[f].ctypes.data for f in ("x", "v", "C", "F")],
+                                    mpm.MEM_HOST)
+            assert st == 0
+            for f in shapes:
+                assert np.array_equal(arrs[f], ref[f]), (scene, f)
+            # write new values from pinned arrays, one field alone and then all four
+            vals = {"x": (sc["x"] + 0.001 * g.random((N, 3))).astype(np.float32),
+                    "v": (0.1 * g.normal(size=(N, 3))).astype(np.float32),
+                    "C": (0.1 * g.normal(size=(N, 3, 3))).astype(np.float32),
+                    "F": (np.eye(3) + 0.01 * g.normal(size=(N, 3, 3))).astype(np.float32)}
+            arrs["v"][...] = vals["v"]
+            assert mpm.mpm_write_state(sim.h, scene, masks["v"], [arrs["v"].ctypes.data], mpm.MEM_HOST) == 0
+            assert np.array_equal(sim.read_state(scene, ("v",))["v"], vals["v"])
+            for f in shapes:
+                arrs[f][...] = vals[f]
+            assert mpm.mpm_write_state(sim.h, scene, 15, [arrs[f].ctypes.data for f in ("x", "v", "C", "F")],
+                                       mpm.MEM_HOST) == 0
+            out = sim.read_state(scene)
+            for f in shapes:
+                assert np.array_equal(out[f], vals[f]), (scene, f)
+        # the other scene is untouched by these writes; substeps still run
+        sim.substep(1e-4, 2)
+        assert sim.error_bits(0) == 0 and sim.error_bits(1) == 0
+
+
 def test_out_of_domain_reported():
     sc = small_cube(2, (0.0, 0.5, 0.5))  # first layer's base cell is -1
     with mpm.from_workload(sc) as sim:
