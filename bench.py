@@ -35,6 +35,8 @@ if ROOT not in sys.path:
 METRIC = "particle-substeps/s at 1M particles FP32"
 UNIT = "particle-substeps/s"
 SUBSTEPS_PER_STEP = 25
+# scan, scatter, P2G, grid update, accumulator reset, G2P (the block has no rigid)
+KERNELS_PER_SUBSTEP = 6
 TRAJECTORY_STEPS = 20  # 20 x 25 = the block's 500-substep trajectory
 FALL_SUBSTEPS = 150    # the block is still falling (F close to I) before this substep
 
@@ -432,11 +434,12 @@ def run_ours(args):
                                   f"state (fall, impact, plastic flow); {restarts} restart(s) inside the timed region"),
                        "l2": "working set > 129 MB L2 between iterations (no flush)",
                        "launch": (f"per step: mpm_substep(dt, {SUBSTEPS_PER_STEP}) = {graphs} CUDA graph replay(s) "
-                                  f"of up to {chunk} substeps, 5 kernels per substep"
+                                  f"of up to {chunk} substeps, {KERNELS_PER_SUBSTEP} kernels per substep"
                                   + "; the first substep runs directly after the key kernel of the initial "
                                   "state" + ("" if restarts == 0 else "; each restart adds 4 state-write kernels "
                                              "and the key kernel"))},
-            "gpu_launches": 5 * total_substeps + 1 + restarts * (4 + 1), "clocks": clk, "roofline": roofline}
+            "gpu_launches": KERNELS_PER_SUBSTEP * total_substeps + 1 + restarts * (4 + 1), "clocks": clk,
+            "roofline": roofline}
     if tuned:
         line["config"]["autotuned"] = tuned
 
