@@ -35,7 +35,7 @@ if ROOT not in sys.path:
 METRIC = "particle-substeps/s at 1M particles FP32"
 UNIT = "particle-substeps/s"
 SUBSTEPS_PER_STEP = 25
-# scan, scatter, P2G, grid update, accumulator reset, G2P (the block has no rigid)
+# scan, scatter, P2G, grid update, accumulator reset, G2P
 KERNELS_PER_SUBSTEP = 6
 TRAJECTORY_STEPS = 20  # 20 x 25 = the block's 500-substep trajectory
 FALL_SUBSTEPS = 150    # the block is still falling (F close to I) before this substep

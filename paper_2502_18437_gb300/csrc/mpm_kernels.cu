@@ -8,7 +8,8 @@
 //              registers into shared-memory 6^3 node windows per brick, flushed
 //              to HBM with vector atomics; leaves the permutation in cell order
 //   k_grid     grid update (Eq. 3), rigid contact (Sec. IV, Eq. 11, Eq. 12),
-//              domain walls, reset of the P2G accumulator
+//              domain walls (k_grid_plain where no scene has a rigid)
+//   k_grid_clear  reset of the P2G accumulator
 //   k_g2p      G2P (Eq. 4, Eq. 9, Eq. 10) with the 2x2x2-brick velocity halo
 //              staged by bulk-copy TMA, plasticity, next brick key + rank
 #include <cstdint>
@@ -848,9 +849,9 @@ __device__ void flush_impulse(const StepArgs& a, const float* simp, int scene, i
 // Rigids of a scene are staged in shared memory (posed at the scene's clock).
 // Grid update of node nid of node brick B (Eq. 3, contact, walls), clearing
 // the P2G accumulator; rigid impulses are summed into simp (shared).
-// CLEAR: reset the node's P2G accumulator after reading it (k_grid_plain leaves
-// that to k_grid_clear, which is faster than loading and clearing in one kernel).
-template <bool EXT, bool CLEAR = true>
+// The node's P2G accumulator is reset afterwards by k_grid_clear: loading and
+// clearing the freshly reduced lines in one kernel measured far slower.
+template <bool EXT>
 __device__ __forceinline__ void grid_node(const StepArgs& a, int B, int scene, int nid, int lane, const RigidCur* rig,
                                           int nr, float* simp)
 {
@@ -863,7 +864,6 @@ __device__ __forceinline__ void grid_node(const StepArgs& a, int B, int scene, i
     const int gk = bz * 4 + (nid & 3);
     const int node = B * 64 + nid;
     const float4 g = a.G[node];
-    if (CLEAR) a.G[node] = make_float4(0.f, 0.f, 0.f, 0.f);
     float3 v = f3(0.f, 0.f, 0.f);
     const float dxs = 1.0f / (float)n;
     float dpr[kMaxRigids][3];
@@ -921,10 +921,7 @@ __device__ __forceinline__ void grid_node(const StepArgs& a, int B, int scene, i
 
 // Grid update of a launch whose scenes have no rigid: no staging and no impulse
 // sums, so a budget of 32 registers holds twice the resident CTAs of k_grid and
-// the node bricks of a 1M-particle block are taken in one round.  The
-// accumulator is reset afterwards by k_grid_clear: loading and clearing it in one
-// kernel measured slower (13.4 us against 11.5 us for the two, the substep 0.1519
-// against 0.1475 ms at 1M particles).
+// the node bricks of a 1M-particle block are taken in one round.
 __global__ void __launch_bounds__(kGridThreads, 8) k_grid_plain(StepArgs a)
 {
     const int tid = threadIdx.x, lane = tid & 31, grp = tid >> 6, nid = tid & 63;
@@ -932,12 +929,15 @@ __global__ void __launch_bounds__(kGridThreads, 8) k_grid_plain(StepArgs a)
     for (int base = blockIdx.x * 4; base < n_nact; base += gridDim.x * 4) {
         const int item = base + grp;
         if (item < n_nact)
-            grid_node<false, false>(a, a.sb.nact_brick[item], a.sb.nact_scene[item], nid, lane, nullptr, 0, nullptr);
+            grid_node<false>(a, a.sb.nact_brick[item], a.sb.nact_scene[item], nid, lane, nullptr, 0, nullptr);
     }
 }
 
-// Reset of the P2G accumulator of the active node bricks, after k_grid_plain has
-// read it.
+// Reset of the P2G accumulator of the active node bricks once the grid update
+// has read it.  Loading and clearing the lines that P2G's reductions just wrote
+// in one kernel measured far slower than two kernels: 13.4 against 11.5 us per
+// substep for the 1M block without rigids, 0.138 against 0.047 ms for the 256
+// batched scenes with their blades.
 __global__ void __launch_bounds__(kGridThreads, 8) k_grid_clear(StepArgs a)
 {
     const int grp = threadIdx.x >> 6, nid = threadIdx.x & 63;
@@ -1816,12 +1816,10 @@ int occupancy_p2g_std()
 
 cudaError_t launch_grid(const StepArgs& a, cudaStream_t s)
 {
-    if (!a.any_rigid) {
-        k_grid_plain<<<a.grid_plain_ctas, kGridThreads, 0, s>>>(a);
-        k_grid_clear<<<a.grid_plain_ctas, kGridThreads, 0, s>>>(a);
-    }
+    if (!a.any_rigid) k_grid_plain<<<a.grid_plain_ctas, kGridThreads, 0, s>>>(a);
     else if (a.rigid_ext) k_grid<true><<<a.grid_ctas, kGridThreads, 0, s>>>(a);
     else k_grid<false><<<a.grid_ctas, kGridThreads, 0, s>>>(a);
+    k_grid_clear<<<a.grid_plain_ctas, kGridThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
