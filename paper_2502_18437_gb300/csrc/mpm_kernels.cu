@@ -138,8 +138,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(StepArgs a)
             c[k] = 0;
             if (b < b1) {
                 c[k] = __ldcg(&sb.cnt[b]);
-                const int flag = __ldcg(&sb.nflag[b]);
-                if (flag) sb.nflag[b] = 0;  // consumed
+                const int flag = __ldcg(&sb.nflag[b]);  // reset by k_grid_clear
                 if (c[k] > 0) pf |= 1u << k;
                 if (c[k] >= kBigBrick) bf |= 1u << k;
                 if (flag) nf |= 1u << k;  // a non-empty brick always flags itself
@@ -933,8 +932,8 @@ __global__ void __launch_bounds__(kGridThreads, 8) k_grid_plain(StepArgs a)
     }
 }
 
-// Reset of the P2G accumulator of the active node bricks once the grid update
-// has read it.  Loading and clearing the lines that P2G's reductions just wrote
+// Reset of the P2G accumulator and of the node-brick flags of the active node
+// bricks once the grid update and the scan have read them.  Loading and clearing the lines that P2G's reductions just wrote
 // in one kernel measured far slower than two kernels: 13.4 against 11.5 us per
 // substep for the 1M block without rigids, 0.138 against 0.047 ms for the 256
 // batched scenes with their blades.
@@ -944,7 +943,11 @@ __global__ void __launch_bounds__(kGridThreads, 8) k_grid_clear(StepArgs a)
     const int n_nact = a.sb.counters[CTR_N_NACT];
     for (int base = blockIdx.x * 4; base < n_nact; base += gridDim.x * 4) {
         const int item = base + grp;
-        if (item < n_nact) a.G[a.sb.nact_brick[item] * 64 + nid] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (item < n_nact) {
+            const int B = a.sb.nact_brick[item];
+            a.G[B * 64 + nid] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (nid == 0) a.sb.nflag[B] = 0;  // the scan has read it (resetting it there was slower)
+        }
     }
 }
 

@@ -19,7 +19,7 @@ struct SortBufs {
     unsigned char* scell; // [cap] sorted slot -> base cell inside its brick (the key's low 6 bits)
     int* cnt;       // [bricks] particles per brick (next substep)
     int* nflag;     // [bricks] node brick touched by a particle brick's stencil (set by the
-                    // key producers, consumed and cleared by the scan)
+                    // key producers, read by the scan, cleared by k_grid_clear)
     int* off;       // [bricks] first slot of each active brick
     int* act_brick; // [bricks] active particle bricks
     int* act_start;
