@@ -210,13 +210,18 @@ def implementation_bytes(N, bricks, active_nodes, pp_mat=False):
 
 def kernel_source_digest():
     """Digest of the CUDA sources, to tell whether a recorded ncu figure still
-    describes the kernels that run."""
+    describes the kernels that run.  Whole-line comments and blank lines are left
+    out, so that editing documentation does not retire a capture; any change to
+    a line of code does."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2502_18437_gb300", "csrc")
     for f in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))):
         h.update(os.path.basename(f).encode())
         with open(f, "rb") as fh:
-            h.update(fh.read())
+            for line in fh:
+                t = line.strip()
+                if t and not t.startswith(b"//"):
+                    h.update(line.rstrip() + b"\n")
     return h.hexdigest()[:16]
 
 

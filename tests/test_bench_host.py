@@ -58,6 +58,11 @@ def test_source_digest_changes_with_any_kernel_source(tmp_path, monkeypatch):
     d1 = bench.kernel_source_digest()
     (csrc / "notes.txt").write_text("not a source")
     assert d0 != d1 and bench.kernel_source_digest() == d1
+    # whole-line comments and blank lines are documentation, not kernel code
+    (csrc / "b.cuh").write_text("// a note\n\nheader B changed\n   // another note\n")
+    assert bench.kernel_source_digest() == d1
+    (csrc / "b.cuh").write_text("header B changed  // a trailing comment is part of the line\n")
+    assert bench.kernel_source_digest() != d1
 
 
 def test_algorithmic_bytes_per_unit():
