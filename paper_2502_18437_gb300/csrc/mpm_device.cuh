@@ -159,6 +159,8 @@ __device__ __forceinline__ float det3(const float F[9])
 
 // ------------------------------------------------------------- 3x3 SVD
 //
+// (The adjoint's decomposition; the forward constitutive update uses the
+// closed-form sym_eigen3 below.)
 // Rotation-variant SVD F = U diag(s) V^T (det U = det V = +1, s sorted by
 // decreasing magnitude, s[2] < 0 when det F < 0) in FP32, after McAdams et al.
 // 2011 ("Computing the SVD of 3x3 matrices with minimal branching"): cyclic

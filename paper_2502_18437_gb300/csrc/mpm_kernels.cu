@@ -1226,10 +1226,11 @@ __device__ __forceinline__ void linearize_window(const float4* vw, float4* lin)
     }
 }
 
-// MINB = CTAs per SM the registers must allow (768/BLOCK: 80 registers;
-// 1024/BLOCK: 64 registers, more warps in flight).  SOLIDS: some scene of the
-// launch has a rigid, so particles may need the push-out (a separate variant:
-// its extra live registers would make the 64-register build spill).
+// MINB = CTAs per SM the registers must allow: the larger budget (7 at 128
+// threads, 72 registers; 3 at 256, 80; 1 at 512) or 1024/BLOCK (64 registers,
+// more warps in flight).  SOLIDS: some scene of the launch has a sphere or a
+// box, so particles may need the push-out (a separate variant: its extra live
+// registers would make the plain build spill).
 template <int BLOCK, int MINB, int FLAGS>
 __global__ void __launch_bounds__(BLOCK, MINB) k_g2p(StepArgs a)
 {
