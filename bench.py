@@ -52,6 +52,9 @@ def parse():
     p.add_argument("--autotune", action="store_true")
     p.add_argument("--profile-substeps", type=int, default=0,
                    help="run this many substeps with direct launches and exit (the command profiles use)")
+    p.add_argument("--profile-batched-substeps", type=int, default=0,
+                   help="run the 256-scene batched workload for this many substeps with direct launches "
+                        "(P2G passes of 576, 128-thread 64-register G2P) and exit")
     return p.parse_args()
 
 
@@ -349,6 +352,19 @@ def run_ours(args):
         dist.barrier()
     mpm.lib()
 
+    if args.profile_batched_substeps:
+        # the command of the batched ncu summary under profiles/: direct launches, no timing
+        bstream = torch.cuda.Stream()
+        bsim = mpm.from_scenes(workloads.batched_scenes(), stream=bstream.cuda_stream)
+        for k, v in (("use_graphs", 0), ("p2g_chunk", 576), ("g2p_threads", 128), ("g2p_regs64", 1)):
+            bsim.set_option(k, v)
+        bsim.substep(1e-4, args.profile_batched_substeps)
+        errs = [bsim.error_bits(s) for s in range(256)]
+        bsim.close()
+        if rank == 0:
+            print(json.dumps({"profile_batched_substeps": args.profile_batched_substeps, "errors": sum(errs)}),
+                  flush=True)
+        return
     sc = workloads.tissue_block(N=args.particles)
     N, n, dt = len(sc["x"]), sc["n"], sc["dt"]
     stream = torch.cuda.Stream()
