@@ -253,12 +253,19 @@ int mpm_substep(mpm_ctx* ctx, float dt, int n_substeps);
  * (one buffer per set bit of `fields`, in increasing bit order).  This is the
  * paper's blocking Scene::fetchResults.  Returns the scene's sticky device
  * error as an MPM_ERR_* code if one is set (the data is still copied).
+ * Host buffers that are page-locked and mapped (cudaHostAlloc, pinned torch
+ * tensors) receive X, V, C, F from one kernel writing them over the host link;
+ * other host memory is filled through a device staging buffer.
  * Errors: INVALID_ARGUMENT, TIMEOUT, CUDA, OUT_OF_DOMAIN, NONFINITE, INVERTED. */
 int mpm_read_state(mpm_ctx* ctx, int scene, uint32_t fields, void* const* dst, int mem);
 
 /* Overwrite fields X, V, C, F of `scene`'s particles from src[k] (id order,
  * one buffer per set bit, increasing bit order); the checkpoint-restore
- * counterpart of mpm_read_state.  Enqueued; Errors: INVALID_ARGUMENT, CUDA. */
+ * counterpart of mpm_read_state.  Device sources: enqueued.  Host sources:
+ * the call returns (bounded wait) once they have been read, so the caller may
+ * reuse them; page-locked, mapped ones are read by one kernel over the host
+ * link, other host memory through a device staging buffer.
+ * Errors: INVALID_ARGUMENT, TIMEOUT, CUDA. */
 int mpm_write_state(mpm_ctx* ctx, int scene, uint32_t fields, const void* const* src, int mem);
 
 /* Wait (bounded) and copy the node velocity and mass after the last grid
@@ -278,8 +285,8 @@ int mpm_scene_count(mpm_ctx* ctx, int scene, int64_t* count);
  * stream, then reports, for the substeps run since the last reset with
  * MPM_OPT_PHASE_TIMING on, the summed device time in milliseconds of each
  * phase: ms[0] sort (scan + scatter), ms[1] P2G (zero for fused substeps that
- * reuse the previous substep's scatter), ms[2] grid update, ms[3] G2P or the
- * fused G2P + P2G;
+ * reuse the previous substep's scatter), ms[2] grid update and the reset of
+ * the P2G accumulator, ms[3] G2P or the fused G2P + P2G;
  * *n_substeps the number of substeps timed; active[0] / active[1] the numbers
  * of active particle bricks / node bricks of the last substep (all scenes of
  * the last launch group).  reset != 0 clears the sums after reading.
